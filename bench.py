@@ -1,0 +1,486 @@
+#!/usr/bin/env python
+"""Benchmark of the regular-force hot path (one JSON line on stdout).
+
+A step is one pass of the whole path on one GPU: predict all j-particles to
+the block time (nb_predict) and compute the regular force, jerk and neighbour
+lists of the active set (nb_regular_force), inputs resident in HBM.  The
+workload is the paper-scale cluster: a Kroupa-IMF Plummer sphere, N = 131072,
+every particle active, ~100 neighbours, list capacity 256, two-float (mixed)
+form.  The FP64 and plain FP32 forms of the same step are timed beside it.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+With N > 1 (launched by torch.distributed.run) every rank runs its own
+replica on its own GPU (independent problems: weak scaling, no collective on
+the data path); value is the interactions of all ranks over the slowest rank's
+time.  --impl reference times the FP64 CPU oracle on bounded samples of the
+same workload (rank 0 only).
+"""
+from __future__ import annotations
+
+import argparse
+import glob
+import hashlib
+import json
+import os
+import re
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = ("regular-force interactions/s and % FP32 peak at N=131072, mixed vs FP64 form, "
+          "rel err ≤1e-6")
+FLOPS_PER_INTERACTION = 60       # convention for one force + jerk interaction
+L2_FLUSH_BYTES = 256 << 20       # > 129 MB L2
+PROFILE = os.path.join(ROOT, "profiles", "regf_mixed_n131072.md")
+
+
+def parse_args():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--mode", default="mixed", choices=["mixed", "fp64", "fp32"])
+    ap.add_argument("--n-act", type=int, default=0, help="active particles (0 = all)")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-forms", action="store_true", help="skip the FP64/FP32 side measurements")
+    ap.add_argument("--cpu-sample", type=int, default=4096, help="active particles in the oracle sample")
+    return ap.parse_args()
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+def workload(n_act):
+    from paper_1205_1222_gb300 import inputs
+    w = inputs.cached(inputs.config3)
+    if n_act and n_act < w.n:
+        w = inputs.subset(w, n_act, 3)
+    return w
+
+
+def describe(w, mode):
+    return {
+        "workload": f"Kroupa-IMF Plummer sphere N={w.n}, n_act={w.n_act}, ~100 neighbours, cap {w.cap}, "
+                    f"seed 3, steps 2^-3..2^-12, {mode} form",
+        "N": w.n, "n_act": w.n_act, "cap": w.cap, "mode": mode, "neighbour_criterion": "|R| < h",
+        "interactions_per_step": w.n * w.n_act,
+        "l2": "flushed between timed steps (256 MB device write outside the timed events)",
+    }
+
+
+# ---------------------------------------------------------------- clocks
+
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device):
+        self.device = device
+        self.proc = None
+        self.path = None
+
+    def __enter__(self):
+        try:
+            fd, self.path = tempfile.mkstemp(prefix="nbclk", suffix=".csv")
+            self.f = os.fdopen(fd, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                                          "-lms", "200", "-i", str(self.device)], stdout=self.f,
+                                         stderr=subprocess.DEVNULL)
+            time.sleep(0.3)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+        return self
+
+    def __exit__(self, *exc):
+        if self.proc is not None:
+            time.sleep(0.25)
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+            self.f.close()
+
+    def summary(self):
+        if self.proc is None or not self.path:
+            return None
+        rows = []
+        for line in open(self.path):
+            p = [s.strip() for s in line.split(",")]
+            if len(p) < 9:
+                continue
+            try:
+                rows.append((float(p[1]), float(p[2]), p[5], p[6], p[7], p[8]))
+            except ValueError:
+                continue
+        os.unlink(self.path)
+        if not rows:
+            return None
+        mx = max(r[1] for r in rows)
+        busy = [r for r in rows if r[0] > 0.5 * mx] or rows
+        reasons = set()
+        for r in rows:
+            for name, flag in zip(("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"),
+                                  r[2:]):
+                if flag.lower() == "active":
+                    reasons.add(name)
+        return {"sm_mhz": statistics.median(r[0] for r in busy), "sm_max_mhz": mx,
+                "reasons": sorted(reasons), "samples": len(rows)}
+
+
+def rejected(clk):
+    if not clk:
+        return False
+    bad = {"hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown"}
+    if bad & set(clk["reasons"]):
+        return True
+    return clk["sm_mhz"] < 0.5 * clk["sm_max_mhz"] and not clk["reasons"]
+
+
+# -------------------------------------------------------------- helpers
+
+def kernel_source_hash():
+    h = hashlib.sha256()
+    for p in sorted(glob.glob(os.path.join(ROOT, "paper_1205_1222_gb300", "csrc", "*"))):
+        h.update(open(p, "rb").read())
+    return h.hexdigest()[:16]
+
+
+def profiled_traffic():
+    """DRAM bytes per launch from the committed ncu summary, if it was taken
+    on the current kernel sources (else None)."""
+    if not os.path.exists(PROFILE):
+        return None
+    text = open(PROFILE).read()
+    mh = re.search(r"kernel_source_hash:\s*([0-9a-f]+)", text)
+    mt = re.search(r"traffic_bytes_per_launch:\s*([0-9.eE+]+)", text)
+    if not mh or not mt or mh.group(1) != kernel_source_hash():
+        return None
+    return float(mt.group(1))
+
+
+def fp32_peak_tflops(sm_count, mhz):
+    # 128 FP32 lanes per SM, 2 flops per fused multiply-add
+    return sm_count * 128 * 2 * mhz * 1e6 / 1e12
+
+
+def max_sm_mhz():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        try:
+            return float(json.load(open(p))["sm_max_mhz"]), "MEASURED_PEAKS.json sm_max_mhz"
+        except Exception:
+            pass
+    return 2070.0, "nominal maximum SM clock"
+
+
+def max_over_ranks(vals, device):
+    """Element-wise maximum of per-rank timings (the slowest rank sets the pace)."""
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor(vals, dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return [float(x) for x in t.cpu()]
+
+
+def job_value(interactions_per_rank, world, ms_max):
+    """Whole-job throughput: all ranks' interactions over the slowest rank's step time."""
+    return interactions_per_rank * world / (ms_max / 1e3)
+
+
+# -------------------------------------------------------------- GPU arm
+
+class Runner:
+    """Device-resident inputs and outputs of one workload, and one step."""
+
+    def __init__(self, w, mode, device):
+        import numpy as np
+        import torch
+
+        from paper_1205_1222_gb300 import Context, binding as B, mode_id
+        self.B, self.torch, self.np = B, torch, np
+        self.w, self.mode, self.device = w, mode_id(mode), device
+        self.ctx = Context(w.n, device=device)
+        dv = lambda a, dt=torch.float64: torch.as_tensor(np.ascontiguousarray(a), dtype=dt, device=f"cuda:{device}")
+        self.d = {k: dv(getattr(w, k)) for k in ("x0", "v0", "a0", "adot0", "m", "t0", "h")}
+        self.d["act"] = dv(w.act, torch.int32)
+        self.out = self.ctx.alloc_outputs(w.n_act, w.cap)
+        self.stream = torch.cuda.current_stream(device)
+        self.form = B.MODE_FORM[self.mode]
+        self.launches = 0
+
+    def predict(self):
+        d = self.d
+        self.B.nb_predict(self.ctx.h, 0, self.w.n, d["x0"], d["v0"], d["a0"], d["adot0"], d["m"], d["t0"],
+                          self.w.t, self.form, self.stream)
+        self.launches += 1
+
+    def force(self):
+        d, o = self.d, self.out
+        self.B.nb_regular_force(self.ctx.h, 0, self.w.n, self.w.n_act, d["act"], d["h"], None, self.w.cap,
+                                self.mode, o["F"], o["J"], None, o["nnb"], o["list"], o["ovf"], self.stream)
+        self.launches += self.ctx.last_launches()
+
+    def timed(self, steps, flush):
+        torch = self.torch
+        ev = [[torch.cuda.Event(enable_timing=True) for _ in range(3)] for _ in range(steps)]
+        for s in range(steps):
+            flush.zero_()
+            ev[s][0].record(self.stream)
+            self.predict()
+            ev[s][1].record(self.stream)
+            self.force()
+            ev[s][2].record(self.stream)
+        torch.cuda.synchronize(self.device)
+        step_ms = [e[0].elapsed_time(e[2]) for e in ev]
+        force_ms = [e[1].elapsed_time(e[2]) for e in ev]
+        return step_ms, force_ms
+
+    def outputs(self):
+        return {k: v.cpu().numpy() for k, v in self.out.items() if v is not None}
+
+    def close(self):
+        self.ctx.close()
+
+
+def e2e_measure(w, mode, device, steps):
+    """The same step through nb_step_host: host (pinned) inputs in, host outputs out."""
+    import numpy as np
+    import torch
+
+    from paper_1205_1222_gb300 import Context, binding as B, mode_id
+    pin = lambda a, dt=torch.float64: torch.as_tensor(np.ascontiguousarray(a), dtype=dt).pin_memory()
+    hx = {k: pin(getattr(w, k)) for k in ("x0", "v0", "a0", "adot0", "m", "t0", "h")}
+    act = pin(w.act, torch.int32)
+    F = torch.empty((w.n_act, 3), dtype=torch.float64).pin_memory()
+    J = torch.empty_like(F)
+    nnb = torch.empty(w.n_act, dtype=torch.int32).pin_memory()
+    lst = torch.empty((w.n_act, w.cap), dtype=torch.int32).pin_memory()
+    ovf = torch.empty(w.n_act, dtype=torch.uint8).pin_memory()
+    h2d = sum(t.numel() * t.element_size() for t in list(hx.values()) + [act])
+    d2h = sum(t.numel() * t.element_size() for t in (F, J, nnb, lst, ovf))
+    with Context(w.n, device=device) as ctx:
+        st = torch.cuda.current_stream(device)
+
+        def step():
+            B.nb_step_host(ctx.h, w.n, hx["x0"], hx["v0"], hx["a0"], hx["adot0"], hx["m"], hx["t0"], w.t, w.n_act,
+                           act, hx["h"], None, w.cap, mode_id(mode), F, J, None, nnb, lst, ovf, st)
+        step()
+        step()
+        t0 = time.perf_counter()
+        for _ in range(steps):
+            step()
+        dt = (time.perf_counter() - t0) / steps
+    return {"value": w.n * w.n_act / dt, "unit": "interactions/s", "ms_per_step": dt * 1e3,
+            "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h),
+            "api": "nb_step_host (pinned host buffers, copies inside the timed call)"}
+
+
+def accuracy(g, o, rows, cap):
+    """Max / RMS relative error per output and list mismatches on the sampled rows."""
+    import numpy as np
+
+    def rel(a, b):
+        nb = np.linalg.norm(b, axis=1)
+        return np.linalg.norm(a - b, axis=1) / np.where(nb > 0, nb, 1.0)
+    eF = rel(g["F"][rows], o["F"])
+    eJ = rel(g["J"][rows], o["J"])
+    k = np.minimum(o["nnb"], cap)
+    filled = np.arange(cap)[None, :] < k[:, None]
+    bad = (g["nnb"][rows] != o["nnb"]) | np.any(np.where(filled, g["list"][rows], -1) !=
+                                               np.where(filled, o["list"], -1), axis=1)
+    return {"F_max": float(eF.max()), "F_rms": float(np.sqrt((eF ** 2).mean())),
+            "J_max": float(eJ.max()), "J_rms": float(np.sqrt((eJ ** 2).mean())),
+            "list_mismatches": int(bad.sum()), "sampled": int(len(rows))}
+
+
+def cpu_baseline(w, sample):
+    """The FP64 oracle, as it stands, on a bounded sample of the active set."""
+    import numpy as np
+
+    import oracle
+    rows = np.sort(np.random.default_rng(12345).choice(w.n_act, min(sample, w.n_act), replace=False))
+    x, v = oracle.predict(w.x0, w.v0, w.a0, w.adot0, w.t0, w.t)
+    threads = oracle.default_threads()
+    t0 = time.perf_counter()
+    o = oracle.regular(x, v, w.m, w.act[rows], w.h[rows], cap=w.cap, threads=threads)
+    dt = time.perf_counter() - t0
+    base = {"value": len(rows) * w.n / dt, "unit": "interactions/s", "cores": threads, "kind": "oracle",
+            "sample": f"{len(rows)} sampled active particles x all {w.n} j-particles "
+                      f"({len(rows) * w.n:.3g} interactions, FP64 C, OpenMP over i, {dt:.2f} s wall)"}
+    return base, o, rows
+
+
+def run_ours(args):
+    import numpy as np
+    import torch
+
+    rank, world, local = dist_env()
+    device = local if world > 1 else 0
+    torch.cuda.set_device(device)
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", device))
+    from paper_1205_1222_gb300 import build
+    if rank == 0:
+        build.build()
+    if world > 1:
+        torch.distributed.barrier()
+    w = workload(args.n_act)
+    r = Runner(w, args.mode, device)
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=f"cuda:{device}")
+    for _ in range(max(args.warmup, 3)):
+        r.predict()
+        r.force()
+    torch.cuda.synchronize(device)
+    st = r.ctx.sync_status()
+    assert st == 0, f"device status {st}"
+
+    def region():
+        if world > 1:
+            torch.distributed.barrier()
+        torch.cuda.synchronize(device)
+        r.launches = 0
+        with ClockSampler(device) as cs:
+            t0 = time.perf_counter()
+            step_ms, force_ms = r.timed(args.steps, flush)
+            wall = time.perf_counter() - t0
+        if world > 1:
+            torch.distributed.barrier()
+        return step_ms, force_ms, wall, cs.summary()
+
+    step_ms, force_ms, wall, clk = region()
+    remeasured = False
+    if rejected(clk):
+        step_ms, force_ms, wall, clk = region()
+        remeasured = True
+    ms = statistics.mean(step_ms)
+    fms = statistics.mean(force_ms)
+    launches = r.launches
+    if world > 1:
+        ms, fms = max_over_ranks([ms, fms], f"cuda:{device}")
+    inter = w.n * w.n_act
+    value = job_value(inter, world, ms)
+    sm = r.ctx.sm_count()
+    mhz, mhz_src = max_sm_mhz()
+    peak = fp32_peak_tflops(sm, mhz)
+    achieved = FLOPS_PER_INTERACTION * inter / (fms / 1e3) / 1e12
+    g_main = r.outputs()
+    r.close()
+
+    if rank != 0:
+        if world > 1:
+            torch.distributed.barrier()
+            torch.distributed.destroy_process_group()
+        return
+
+    line = {
+        "metric": METRIC, "value": value, "unit": "interactions/s", "n_gpus": world, "steps": args.steps,
+        "warmup": max(args.warmup, 3), "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32" if args.mode != "fp64" else "f64", "data": "synthetic",
+        "config": dict(describe(w, args.mode), parallelism=f"replicas{world}" if world > 1 else "single"),
+    }
+    line["roofline"] = {
+        "bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
+        "traffic": profiled_traffic(),
+        "kernel": "regf_kernel (regular force + jerk + list), one launch per step",
+        "kernel_ms": fms,
+        "peak_basis": f"{sm} SMs x 128 FP32 lanes x 2 flops x {mhz:.0f} MHz ({mhz_src}); "
+                      f"{FLOPS_PER_INTERACTION} flops per interaction",
+    }
+    if clk:
+        line["roofline"]["peak_at_measured_clock"] = fp32_peak_tflops(sm, clk["sm_mhz"])
+        line["roofline"]["frac_at_measured_clock"] = achieved / line["roofline"]["peak_at_measured_clock"]
+    line["gpu_launches"] = launches
+    line["clocks"] = clk
+    if remeasured:
+        line["clocks_remeasured"] = True
+    line["wall_s_timed_region"] = wall
+
+    forms = {}
+    outs = {args.mode: g_main}
+    if not args.no_forms:
+        for mode in ("fp64", "fp32", "mixed"):
+            if mode == args.mode:
+                forms[mode] = {"value": value / world, "ms_per_step": ms, "kernel_ms": fms}
+                continue
+            rr = Runner(w, mode, device)
+            rr.predict(); rr.force()
+            torch.cuda.synchronize(device)
+            k = 2 if mode == "fp64" else args.steps
+            sm_, fm_ = rr.timed(k, flush)
+            forms[mode] = {"value": inter / (statistics.mean(sm_) / 1e3), "ms_per_step": statistics.mean(sm_),
+                           "kernel_ms": statistics.mean(fm_), "steps": k,
+                           "frac_fp32_peak": FLOPS_PER_INTERACTION * inter / (statistics.mean(fm_) / 1e3) / 1e12 / peak}
+            outs[mode] = rr.outputs()
+            rr.close()
+        line["forms"] = forms
+    line["e2e"] = e2e_measure(w, args.mode, device, max(1, min(args.steps, 5)))
+    if not args.no_cpu_baseline:
+        base, o, rows = cpu_baseline(w, args.cpu_sample)
+        line["cpu_baseline"] = base
+        line["accuracy_vs_oracle"] = {m: accuracy(g, o, rows, w.cap) for m, g in outs.items()}
+    if world > 1:
+        torch.distributed.barrier()
+        torch.distributed.destroy_process_group()
+    print(json.dumps(line), flush=True)
+
+
+def run_reference(args):
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return
+    import numpy as np
+
+    import oracle
+    w = workload(args.n_act)
+    x, v = oracle.predict(w.x0, w.v0, w.a0, w.adot0, w.t0, w.t)
+    threads = oracle.default_threads()
+    sample = min(256, w.n_act)
+    rng = np.random.default_rng(7)
+
+    def step():
+        rows = np.sort(rng.choice(w.n_act, sample, replace=False))
+        oracle.predict(w.x0, w.v0, w.a0, w.adot0, w.t0, w.t)
+        oracle.regular(x, v, w.m, w.act[rows], w.h[rows], cap=w.cap, threads=threads)
+    for _ in range(args.warmup):
+        step()
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        step()
+    dt = (time.perf_counter() - t0) / args.steps
+    value = sample * w.n / dt
+    desc = (f"each step: FP64 oracle prediction of all {w.n} j plus the regular force of {sample} sampled "
+            f"active particles ({sample * w.n:.3g} interactions), OpenMP over i")
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "interactions/s", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt * 1e3, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": describe(w, "fp64 oracle"),
+            "cpu_baseline": {"value": value, "unit": "interactions/s", "cores": threads, "kind": "oracle",
+                             "sample": desc},
+            "e2e": {"value": value, "unit": "interactions/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    args = parse_args()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,237 @@
+/*
+ * nbreg.h - C-ABI of the GB300 regular-force library (libnbreg.so).
+ *
+ * The library computes, for the active particles of one block step of an
+ * Ahmad-Cohen (AC) neighbour-scheme N-body integrator, the regular force, its
+ * time derivative (jerk) and the neighbour list, after predicting all
+ * j-particles to the block time (Nitadori & Aarseth 2012, "Accelerating
+ * NBODY6 with Graphics Processing Units"):
+ *   - prediction of the j-particles: Sec. 3.3, step (iii);
+ *   - neighbour criterion |R_ij| < h_i, or with the velocity term
+ *     min(|R_ij|, |R_ij + dtr_i V_ij|) < h_i: Sec. 3.2;
+ *   - regular force F_R,i = sum over j != i outside the sphere of
+ *     m_j R_ij/|R_ij|^3, its derivative m_j [V_ij/|R_ij|^3
+ *     - 3 (R_ij.V_ij) R_ij/|R_ij|^5], and the list
+ *     L_i = { j != i : R_min < h_i }: Sec. 3.3, step (vi);
+ *   - the library boundary itself mirrors the paper's GPUNB calls (send the
+ *     predicted j-set, then compute blocks of i): Sec. 3.4 and Appendix C.
+ * G = 1.  R_ij = x_j - x_i, V_ij = v_j - v_i.
+ *
+ * Conventions shared by every entry point:
+ *   - Every pointer argument is a DEVICE pointer owned by the caller, unless
+ *     the argument is documented as a host pointer.  The library never frees
+ *     caller memory.  The context owns the predicted j-set and the scratch.
+ *   - Vectors are row-major [n][3] FP64 (x, y, z of particle j at 3j..3j+2).
+ *   - Indices are 0-based.  Active indices and list entries are relative to
+ *     the first slot of the j-range a call is given.
+ *   - Calls that take a stream are asynchronous on that stream (NULL is the
+ *     legacy default stream).  They return at once with NB_OK or an argument
+ *     error; errors raised on the device (bad index inside a device array,
+ *     a bounded wait that ran out) are recorded in a device status word and
+ *     surface through nb_sync_status().
+ *   - No exception crosses the boundary; every entry point returns a status.
+ *   - A context is bound to one device and must be used from one host thread
+ *     at a time.
+ */
+#ifndef NBREG_H
+#define NBREG_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* Status codes returned by every entry point. */
+enum nb_status {
+    NB_OK = 0,
+    NB_ERR_ARG = -1,         /* invalid argument (detected on the host)          */
+    NB_ERR_CUDA = -2,        /* a CUDA runtime call failed                        */
+    NB_ERR_NOMEM = -3,       /* device or pinned memory allocation failed         */
+    NB_ERR_TIMEOUT = -4,     /* a bounded device wait ran out (device status)     */
+    NB_ERR_STATE = -5,       /* e.g. the requested precision form was not predicted */
+    NB_ERR_UNSUPPORTED = -6, /* no kernel for this combination                    */
+    NB_ERR_DEVICE_INPUT = -7 /* invalid value found on the device (index, radius) */
+};
+
+/* Precision form of the pairwise arithmetic. */
+enum nb_mode {
+    NB_FP64 = 0,  /* FP64 differences, FP64 pair terms, FP64 sums                   */
+    NB_MIXED = 1, /* two-float (hi+lo) position and velocity differences, FP32 pair  *
+                   * terms, float-float sums per lane, FP64 across lanes and splits  */
+    NB_FP32 = 2   /* plain FP32 differences and pair terms, same sums as NB_MIXED    */
+};
+
+/* Bit mask of the predicted forms nb_predict()/nb_set_predicted() write. */
+enum nb_form_bits { NB_FORM_FP64 = 1, NB_FORM_MIXED = 2, NB_FORM_FP32 = 4, NB_FORM_ALL = 7 };
+
+typedef struct nb_ctx nb_ctx;     /* opaque, library-owned */
+typedef struct nb_plan nb_plan;   /* opaque, library-owned */
+typedef void *nb_stream_t;        /* a cudaStream_t */
+
+/* Kernel tiling of the regular-force kernel (chosen by the autotuner). */
+typedef struct nb_kcfg {
+    int32_t warps;      /* warps per CTA; each warp owns `ipw` active particles        */
+    int32_t ipw;        /* active particles per warp (the i-tile of a warp)             */
+    int32_t jtile;      /* j-particles per shared-memory tile                            */
+    int32_t split;      /* j-tiles per work item; 0 = choose from the grid size          */
+} nb_kcfg;
+
+/* One independent cluster of a batched call (host struct; the pointers in it
+ * are device pointers with the meaning of the nb_regular_force arguments). */
+typedef struct nb_cluster {
+    int64_t j_begin;       /* first slot of this cluster in the context's j-set */
+    int64_t n_j;           /* number of j-particles of the cluster              */
+    int32_t n_act;         /* active particles                                   */
+    int32_t cap;           /* list capacity per active particle                  */
+    const int32_t *act;    /* [n_act] indices in [0, n_j)                        */
+    const double *h;       /* [n_act] neighbour radii, >= 0                      */
+    const double *dtr;     /* [n_act] regular steps, or NULL (plain criterion)   */
+    double *F;             /* [n_act][3] regular force                           */
+    double *J;             /* [n_act][3] regular jerk                            */
+    double *pot;           /* [n_act] sum of m_j/|R_ij| over the regular set, or NULL */
+    int32_t *nnb;          /* [n_act] true neighbour count                       */
+    int32_t *list;         /* [n_act][cap] ascending neighbour indices, or NULL if cap == 0 */
+    uint8_t *ovf;          /* [n_act] 1 when nnb > cap                           */
+} nb_cluster;
+
+/* Open a context on CUDA device `device` for up to n_max j-particles
+ * (~ GPUNB_OPEN, Appendix C).  Allocates the predicted j-set (160 bytes per
+ * slot for all three forms) and the device status word.  *out is NULL on
+ * failure.  Returns NB_ERR_ARG (n_max <= 0, bad device), NB_ERR_NOMEM or
+ * NB_ERR_CUDA. */
+int nb_create(nb_ctx **out, int device, int64_t n_max);
+
+/* Release everything the context owns (~ GPUNB_CLOSE).  NULL is a no-op.
+ * Synchronises the device first. */
+void nb_destroy(nb_ctx *ctx);
+
+/* Predict j-particles to the block time t and store them in slots
+ * [offset, offset + n) of the context's j-set (Sec. 3.3 step (iii); the
+ * paper's host predictor followed by GPUNB_SEND, here one kernel):
+ *   dt = t - t0_j,  x = x0 + v0 dt + a0 dt^2/2 + adot0 dt^3/6,
+ *                   v = v0 + a0 dt + adot0 dt^2/2       (FP64).
+ * x0, v0, a0, adot0: [n][3]; m, t0: [n]; all device pointers.
+ * forms: NB_FORM_* bits of the stored copies to write (0 = all): FP64
+ * (x,y,z,m)+(vx,vy,vz,0) as double4; MIXED hi/lo float pairs of position and
+ * velocity with the mass in the hi-position w; FP32 float4 copies.
+ * Errors: NB_ERR_ARG if offset < 0, n < 0, offset + n > n_max, a NULL array
+ * with n > 0. */
+int nb_predict(nb_ctx *ctx, int64_t offset, int64_t n, const double *x0, const double *v0,
+               const double *a0, const double *adot0, const double *m, const double *t0,
+               double t, int forms, nb_stream_t stream);
+
+/* Store already-predicted positions x, velocities v ([n][3]) and masses m
+ * ([n]) in slots [offset, offset + n) (the bare GPUNB_SEND of the paper).
+ * Same errors as nb_predict. */
+int nb_set_predicted(nb_ctx *ctx, int64_t offset, int64_t n, const double *x, const double *v,
+                     const double *m, int forms, nb_stream_t stream);
+
+/* Read back slots [offset, offset + n) of the stored FP64 form: positions x
+ * and velocities v ([n][3], device) and masses m ([n], device; may be NULL).
+ * NB_ERR_STATE if the FP64 form was not written by the last prediction. */
+int nb_get_predicted(nb_ctx *ctx, int64_t offset, int64_t n, double *x, double *v, double *m,
+                     nb_stream_t stream);
+
+/* Regular force, jerk and neighbour list (Sec. 3.3 step (vi), criterion of
+ * Sec. 3.2; ~ GPUNB_REGF).  The j-set is slots [j_begin, j_begin + n_j) of
+ * the context; act[k] in [0, n_j) names active particle k within that range.
+ *   h     [n_act] radii (>= 0, finite); dtr [n_act] regular steps or NULL
+ *   cap   list capacity (>= 0); list is [n_act][cap], may be NULL if cap == 0
+ *   F, J  [n_act][3]; pot [n_act] or NULL; nnb [n_act]; ovf [n_act]
+ * Self is excluded by index.  The list holds the lowest min(nnb, cap)
+ * neighbour indices in ascending order; entries past that are not written.
+ * nnb is the true count, ovf[k] = (nnb[k] > cap).  A pair at exactly |R| = h
+ * is not a neighbour.  Pairs with |R_ij| = 0 (j != i) outside the sphere are
+ * undefined input.  mode: NB_FP64, NB_MIXED or NB_FP32; the matching form
+ * must have been predicted (NB_ERR_STATE otherwise).  May grow the context's
+ * split scratch with cudaMalloc (call nb_reserve() first to avoid that, e.g.
+ * before stream capture).  Errors: NB_ERR_ARG for out-of-range sizes, NULL
+ * outputs, mode; invalid act/h values found on the device set
+ * NB_ERR_DEVICE_INPUT in the status word (those particles get no result). */
+int nb_regular_force(nb_ctx *ctx, int64_t j_begin, int64_t n_j, int32_t n_act,
+                     const int32_t *act, const double *h, const double *dtr, int32_t cap,
+                     int mode, double *F, double *J, double *pot, int32_t *nnb,
+                     int32_t *list, uint8_t *ovf, nb_stream_t stream);
+
+/* Make sure the split scratch holds at least `bytes` (device memory). */
+int nb_reserve(nb_ctx *ctx, size_t bytes);
+
+/* Scratch bytes a call of nb_regular_force with these sizes needs (0 when the
+ * call needs no split).  Host only. */
+size_t nb_scratch_bytes(nb_ctx *ctx, int64_t n_j, int32_t n_act, int32_t cap, int mode);
+
+/* Batched form: the regular-force call for n_clusters independent clusters
+ * (host array `clusters`), all in ONE persistent kernel launch plus one merge
+ * launch.  A plan uploads the cluster table once and owns its scratch, so
+ * nb_plan_run() allocates nothing and can be captured into a CUDA graph.
+ * cfg NULL = the context's configuration for `mode`. */
+int nb_plan_create(nb_ctx *ctx, int32_t n_clusters, const nb_cluster *clusters, int mode,
+                   const nb_kcfg *cfg, nb_plan **out);
+int nb_plan_run(nb_plan *plan, nb_stream_t stream);
+/* Capture nb_plan_run on `stream` into a CUDA graph owned by the plan. */
+int nb_plan_capture(nb_plan *plan, nb_stream_t stream);
+/* Launch the captured graph (NB_ERR_STATE if nb_plan_capture was not called). */
+int nb_plan_launch(nb_plan *plan, nb_stream_t stream);
+void nb_plan_destroy(nb_plan *plan);
+/* Kernel launches one nb_plan_run issues (host only). */
+int nb_plan_launches(const nb_plan *plan);
+
+/* One whole block step through HOST buffers: copy the j-set inputs and the
+ * active set from host memory, predict (only the form `mode` needs), compute
+ * the regular force, copy the results back into host memory and wait for
+ * them.  All array arguments are HOST pointers (pinned memory gives
+ * asynchronous copies).  Same meaning and errors as nb_predict followed by
+ * nb_regular_force on j-range [0, n); also returns the device status. */
+int nb_step_host(nb_ctx *ctx, int64_t n, const double *x0, const double *v0, const double *a0,
+                 const double *adot0, const double *m, const double *t0, double t,
+                 int32_t n_act, const int32_t *act, const double *h, const double *dtr,
+                 int32_t cap, int mode, double *F, double *J, double *pot, int32_t *nnb,
+                 int32_t *list, uint8_t *ovf, nb_stream_t stream);
+
+/* Wait for `stream`, then read and clear the device status word.  Returns
+ * NB_OK, NB_ERR_TIMEOUT, NB_ERR_DEVICE_INPUT or NB_ERR_CUDA. */
+int nb_sync_status(nb_ctx *ctx, nb_stream_t stream);
+
+/* Text for a status code (static storage). */
+const char *nb_strerror(int status);
+
+/* Text of the last error recorded on the context (valid until the next call). */
+const char *nb_last_error(nb_ctx *ctx);
+
+/* Kernel configurations compiled for a mode (the autotuner's search space). */
+int nb_num_kernel_configs(int mode);
+int nb_get_kernel_config(int mode, int index, nb_kcfg *out);
+/* Select the configuration nb_regular_force uses for `mode` (NULL = built-in
+ * default).  NB_ERR_UNSUPPORTED if no compiled kernel matches. */
+int nb_set_kernel_config(nb_ctx *ctx, int mode, const nb_kcfg *cfg);
+int nb_get_active_config(nb_ctx *ctx, int mode, nb_kcfg *out);
+
+/* Timing harness of the autotuner: run nb_regular_force with configuration
+ * `cfg` `reps` times on `stream` after one warm-up and return the mean device
+ * time per call in *ms (CUDA events on that stream). */
+int nb_time_regular_force(nb_ctx *ctx, const nb_kcfg *cfg, int64_t j_begin, int64_t n_j,
+                          int32_t n_act, const int32_t *act, const double *h,
+                          const double *dtr, int32_t cap, int mode, double *F, double *J,
+                          double *pot, int32_t *nnb, int32_t *list, uint8_t *ovf, int reps,
+                          nb_stream_t stream, float *ms);
+
+/* Number of kernels the last nb_regular_force call on this context launched. */
+int nb_last_launches(nb_ctx *ctx);
+
+/* Multiprocessor count of the context's device. */
+int nb_sm_count(nb_ctx *ctx);
+
+/* Test hook for the failure path: bound every device copy wait by wait_ns
+ * nanoseconds (0 = the default of 4 s) and make each copy barrier expect
+ * extra_tx more bytes than are copied (rounded down to a multiple of 16; 0 in
+ * normal use).  With extra_tx > 0 no copy barrier completes, every wait runs
+ * out after wait_ns, the kernels return early and nb_sync_status() reports
+ * NB_ERR_TIMEOUT; the results of such calls are undefined. */
+int nb_debug_set_wait(nb_ctx *ctx, uint64_t wait_ns, uint32_t extra_tx);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* NBREG_H */

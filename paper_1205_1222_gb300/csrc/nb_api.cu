@@ -1,0 +1,875 @@
+// Host side of libnbreg: the C-ABI declared in include/nbreg.h.
+//
+// The context owns the predicted j-set (three stored forms, SoA float4 /
+// double4 streams), the split scratch, a device status word and the host-step
+// staging buffers.  A regular-force call is one persistent kernel launch over
+// work items (i-block x j-split) plus, when the j-range is split, one merge
+// launch; nothing is copied between host and device inside a call.
+#include <algorithm>
+#include <cstdio>
+#include <cstring>
+#include <mutex>
+#include <string>
+#include <vector>
+
+#include <cuda_runtime.h>
+
+#include "nb_aux.cuh"
+#include "nbreg.h"
+
+using nb::ClusterDesc;
+using nb::KernelEntry;
+
+namespace {
+
+constexpr uint64_t kDefaultWaitNs = 4000000000ull;   // 4 s bound on every copy wait
+
+struct DeviceGuard {
+    int prev = -1;
+    bool changed = false;
+    explicit DeviceGuard(int dev)
+    {
+        if (cudaGetDevice(&prev) == cudaSuccess && prev != dev) {
+            changed = cudaSetDevice(dev) == cudaSuccess;
+        }
+    }
+    ~DeviceGuard()
+    {
+        if (changed) cudaSetDevice(prev);
+    }
+};
+
+struct Registry {
+    std::vector<KernelEntry> all;
+    std::vector<int> occ;        // resident CTAs per SM, per entry (-1 = not yet queried)
+    std::mutex mu;
+};
+
+Registry &registry()
+{
+    static Registry r;
+    static std::once_flag once;
+    std::call_once(once, [] {
+        int n = 0;
+        const KernelEntry *e = nb::kernels_fp64(&n);
+        r.all.insert(r.all.end(), e, e + n);
+        e = nb::kernels_mixed(&n);
+        r.all.insert(r.all.end(), e, e + n);
+        e = nb::kernels_fp32(&n);
+        r.all.insert(r.all.end(), e, e + n);
+        r.occ.assign(r.all.size(), -1);
+    });
+    return r;
+}
+
+size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
+
+}  // namespace
+
+struct nb_ctx {
+    int device = 0;
+    int64_t n_max = 0;
+    int sm_count = 0;
+    double4_32a *pos64 = nullptr, *vel64 = nullptr;
+    float4 *mx_hi = nullptr, *mx_lo = nullptr, *mv_hi = nullptr, *mv_lo = nullptr;
+    float4 *pos32 = nullptr, *vel32 = nullptr;
+    int forms_valid = 0;
+    int *d_status = nullptr;
+    void *scratch = nullptr;
+    size_t scratch_bytes = 0;
+    nb_kcfg cfg[3];
+    bool cfg_set[3] = {false, false, false};
+    int last_launches = 0;
+    uint64_t wait_ns = kDefaultWaitNs;
+    uint32_t extra_tx = 0;
+    void *stage = nullptr;   // nb_step_host device staging
+    size_t stage_bytes = 0;
+    std::string err;
+};
+
+struct nb_plan {
+    nb_ctx *ctx = nullptr;
+    int mode = 0;
+    const KernelEntry *e = nullptr;
+    int entry = -1;
+    int grid = 0;
+    int64_t n_items = 0;
+    std::vector<ClusterDesc> descs;
+    ClusterDesc *d_table = nullptr;
+    int64_t *d_item_begin = nullptr;
+    int n_merge = 0;
+    int64_t merge_total = 0;
+    int64_t *d_act_begin = nullptr;
+    int32_t *d_cluster_of = nullptr;
+    void *scratch = nullptr;
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+};
+
+namespace {
+
+int cuda_fail(nb_ctx *ctx, cudaError_t e, const char *what)
+{
+    if (ctx) ctx->err = std::string(what) + ": " + cudaGetErrorString(e);
+    return NB_ERR_CUDA;
+}
+
+#define NB_CUDA(ctx, call)                                                   \
+    do {                                                                     \
+        cudaError_t e_ = (call);                                             \
+        if (e_ != cudaSuccess) return cuda_fail((ctx), e_, #call);           \
+    } while (0)
+
+int mode_forms(int mode) { return mode == NB_FP64 ? NB_FORM_FP64 : mode == NB_MIXED ? NB_FORM_MIXED : NB_FORM_FP32; }
+
+nb_kcfg default_cfg(int mode)
+{
+    Registry &r = registry();
+    for (const auto &e : r.all)
+        if (e.mode == mode && e.flags == 0) return nb_kcfg{e.warps, e.ipw, e.jtile, 0};
+    return nb_kcfg{0, 0, 0, 0};
+}
+
+// Index of the kernel for (mode, cfg, flags); falls back to the mode's default
+// tiling when this tiling has no instantiation with those flags.
+int find_entry(int mode, const nb_kcfg &cfg, int flags)
+{
+    Registry &r = registry();
+    for (size_t i = 0; i < r.all.size(); i++) {
+        const auto &e = r.all[i];
+        if (e.mode == mode && e.flags == flags && e.warps == cfg.warps && e.ipw == cfg.ipw &&
+            e.jtile == cfg.jtile)
+            return static_cast<int>(i);
+    }
+    for (size_t i = 0; i < r.all.size(); i++)
+        if (r.all[i].mode == mode && r.all[i].flags == flags) return static_cast<int>(i);
+    return -1;
+}
+
+int entry_occupancy(nb_ctx *ctx, int idx, int *occ)
+{
+    Registry &r = registry();
+    std::lock_guard<std::mutex> lock(r.mu);
+    if (r.occ[idx] < 0) {
+        const KernelEntry &e = r.all[idx];
+        NB_CUDA(ctx, cudaFuncSetAttribute(e.fn, cudaFuncAttributeMaxDynamicSharedMemorySize, e.smem));
+        int o = 0;
+        NB_CUDA(ctx, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o, e.fn, e.warps * 32, e.smem));
+        if (o < 1) {
+            ctx->err = "kernel does not fit on a multiprocessor";
+            return NB_ERR_UNSUPPORTED;
+        }
+        r.occ[idx] = o;
+    }
+    *occ = r.occ[idx];
+    return NB_OK;
+}
+
+// Fill the tiling fields of one cluster descriptor.
+void tile_cluster(const KernelEntry &e, int occ, int sm, const nb_kcfg *cfg, ClusterDesc &d)
+{
+    const int ipb = e.warps * e.ipw;
+    d.n_iblk = (d.n_act + ipb - 1) / ipb;
+    d.n_tiles = static_cast<int32_t>((static_cast<int64_t>(d.n_j) + e.jtile - 1) / e.jtile);
+    int tps;
+    if (cfg && cfg->split > 0) {
+        tps = cfg->split;
+    } else {
+        // enough work items for ~4 resident CTAs' worth of items per slot,
+        // but at least two tiles per item
+        const int64_t slots = static_cast<int64_t>(sm) * occ;
+        const int64_t want = std::max<int64_t>(1, (4 * slots + d.n_iblk - 1) / std::max(d.n_iblk, 1));
+        tps = static_cast<int>(std::max<int64_t>(2, (d.n_tiles + want - 1) / want));
+    }
+    d.tiles_per_split = std::max(1, tps);
+    d.n_split = d.n_tiles == 0 ? 1 : (d.n_tiles + d.tiles_per_split - 1) / d.tiles_per_split;
+}
+
+// Bytes of split scratch one cluster needs, and the carving of it.
+size_t cluster_scratch(const ClusterDesc &d)
+{
+    if (d.n_split <= 1) return 0;
+    const size_t cells = static_cast<size_t>(d.n_split) * d.n_act;
+    return align_up(cells * 8 * sizeof(double), 256) + align_up(cells * sizeof(int32_t), 256) +
+           align_up(cells * static_cast<size_t>(d.cap) * sizeof(int32_t), 256);
+}
+
+void carve_scratch(ClusterDesc &d, char *base)
+{
+    if (d.n_split <= 1) { d.pF = nullptr; d.pcnt = nullptr; d.plist = nullptr; return; }
+    const size_t cells = static_cast<size_t>(d.n_split) * d.n_act;
+    d.pF = reinterpret_cast<double *>(base);
+    base += align_up(cells * 8 * sizeof(double), 256);
+    d.pcnt = reinterpret_cast<int32_t *>(base);
+    base += align_up(cells * sizeof(int32_t), 256);
+    d.plist = reinterpret_cast<int32_t *>(base);
+}
+
+nb::JSet jset(const nb_ctx *c, int mode)
+{
+    nb::JSet js{};
+    if (mode == NB_FP64) { js.s[0] = c->pos64; js.s[1] = c->vel64; }
+    else if (mode == NB_MIXED) { js.s[0] = c->mx_hi; js.s[1] = c->mx_lo; js.s[2] = c->mv_hi; js.s[3] = c->mv_lo; }
+    else { js.s[0] = c->pos32; js.s[1] = c->vel32; }
+    return js;
+}
+
+int grow_scratch(nb_ctx *ctx, size_t need, cudaStream_t st)
+{
+    if (need <= ctx->scratch_bytes) return NB_OK;
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    if (cudaStreamIsCapturing(st, &cs) == cudaSuccess && cs != cudaStreamCaptureStatusNone) {
+        ctx->err = "split scratch too small during stream capture (call nb_reserve first)";
+        return NB_ERR_STATE;
+    }
+    NB_CUDA(ctx, cudaStreamSynchronize(st));
+    if (ctx->scratch) cudaFree(ctx->scratch);
+    ctx->scratch = nullptr;
+    ctx->scratch_bytes = 0;
+    if (cudaMalloc(&ctx->scratch, need) != cudaSuccess) {
+        cudaGetLastError();
+        ctx->err = "cannot allocate split scratch";
+        return NB_ERR_NOMEM;
+    }
+    ctx->scratch_bytes = need;
+    return NB_OK;
+}
+
+struct Call {
+    int64_t j_begin, n_j;
+    int32_t n_act;
+    const int32_t *act;
+    const double *h, *dtr;
+    int32_t cap;
+    int mode;
+    double *F, *J, *pot;
+    int32_t *nnb, *list;
+    uint8_t *ovf;
+};
+
+int check_call(nb_ctx *ctx, const Call &c)
+{
+    if (!ctx) return NB_ERR_ARG;
+    if (c.mode < NB_FP64 || c.mode > NB_FP32) { ctx->err = "bad mode"; return NB_ERR_ARG; }
+    if (c.j_begin < 0 || c.n_j < 0 || c.j_begin + c.n_j > ctx->n_max || c.n_j > INT32_MAX) {
+        ctx->err = "j-range outside the context";
+        return NB_ERR_ARG;
+    }
+    if (c.n_act < 0 || c.cap < 0) { ctx->err = "negative n_act or cap"; return NB_ERR_ARG; }
+    if (c.n_act > 0) {
+        if (c.n_j == 0) { ctx->err = "active particles with an empty j-range"; return NB_ERR_ARG; }
+        if (!c.act || !c.h || !c.F || !c.J || !c.nnb || !c.ovf) { ctx->err = "NULL array"; return NB_ERR_ARG; }
+        if (c.cap > 0 && !c.list) { ctx->err = "NULL list with cap > 0"; return NB_ERR_ARG; }
+    }
+    if (!(ctx->forms_valid & mode_forms(c.mode))) {
+        ctx->err = "the requested form has not been predicted";
+        return NB_ERR_STATE;
+    }
+    return NB_OK;
+}
+
+ClusterDesc make_desc(const Call &c)
+{
+    ClusterDesc d{};
+    d.j_begin = c.j_begin;
+    d.n_j = static_cast<int32_t>(c.n_j);
+    d.n_act = c.n_act;
+    d.cap = c.cap;
+    d.act = c.act;
+    d.h = c.h;
+    d.dtr = c.dtr;
+    d.F = c.F;
+    d.J = c.J;
+    d.pot = c.pot;
+    d.nnb = c.nnb;
+    d.list = c.list;
+    d.ovf = c.ovf;
+    return d;
+}
+
+int run_single(nb_ctx *ctx, const Call &c, const nb_kcfg *cfg_override, cudaStream_t st)
+{
+    int rc = check_call(ctx, c);
+    if (rc != NB_OK) return rc;
+    ctx->last_launches = 0;
+    if (c.n_act == 0) return NB_OK;
+    DeviceGuard guard(ctx->device);
+    const nb_kcfg cfg = cfg_override ? *cfg_override : (ctx->cfg_set[c.mode] ? ctx->cfg[c.mode] : default_cfg(c.mode));
+    const int flags = (c.dtr ? 1 : 0) | (c.pot ? 2 : 0);
+    const int idx = find_entry(c.mode, cfg, flags);
+    if (idx < 0) { ctx->err = "no kernel for this mode"; return NB_ERR_UNSUPPORTED; }
+    int occ = 0;
+    rc = entry_occupancy(ctx, idx, &occ);
+    if (rc != NB_OK) return rc;
+    const KernelEntry &e = registry().all[idx];
+    ClusterDesc d = make_desc(c);
+    tile_cluster(e, occ, ctx->sm_count, &cfg, d);
+    d.item_begin = 0;
+    rc = grow_scratch(ctx, cluster_scratch(d), st);
+    if (rc != NB_OK) return rc;
+    carve_scratch(d, static_cast<char *>(ctx->scratch));
+
+    nb::RegfParams p{};
+    p.js = jset(ctx, c.mode);
+    p.d0 = d;
+    p.table = nullptr;
+    p.item_begin = nullptr;
+    p.n_clusters = 1;
+    p.n_items = static_cast<int64_t>(d.n_iblk) * d.n_split;
+    p.status = ctx->d_status;
+    p.wait_ns = ctx->wait_ns;
+    p.extra_tx = ctx->extra_tx;
+    const int64_t grid = std::min<int64_t>(p.n_items, static_cast<int64_t>(ctx->sm_count) * occ);
+    void *args[] = {&p};
+    NB_CUDA(ctx, cudaLaunchKernel(e.fn, dim3(static_cast<unsigned>(grid)), dim3(e.warps * 32), args,
+                                  e.smem, st));
+    ctx->last_launches = 1;
+    if (d.n_split > 1) {
+        nb::MergeParams mp{};
+        mp.d0 = d;
+        mp.n_clusters = 1;
+        mp.n_total = d.n_act;
+        nb::launch_merge(mp, st);
+        NB_CUDA(ctx, cudaGetLastError());
+        ctx->last_launches = 2;
+    }
+    return NB_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char *nb_strerror(int s)
+{
+    switch (s) {
+    case NB_OK: return "ok";
+    case NB_ERR_ARG: return "invalid argument";
+    case NB_ERR_CUDA: return "CUDA runtime error";
+    case NB_ERR_NOMEM: return "out of memory";
+    case NB_ERR_TIMEOUT: return "a bounded device wait ran out";
+    case NB_ERR_STATE: return "invalid state (form not predicted, or scratch too small under capture)";
+    case NB_ERR_UNSUPPORTED: return "unsupported configuration";
+    case NB_ERR_DEVICE_INPUT: return "invalid active index or radius found on the device";
+    default: return "unknown status";
+    }
+}
+
+const char *nb_last_error(nb_ctx *ctx) { return ctx ? ctx->err.c_str() : "no context"; }
+
+int nb_create(nb_ctx **out, int device, int64_t n_max)
+{
+    if (!out) return NB_ERR_ARG;
+    *out = nullptr;
+    if (n_max <= 0 || n_max > INT32_MAX) return NB_ERR_ARG;
+    int ndev = 0;
+    if (cudaGetDeviceCount(&ndev) != cudaSuccess || device < 0 || device >= ndev) {
+        cudaGetLastError();
+        return NB_ERR_ARG;
+    }
+    DeviceGuard guard(device);
+    nb_ctx *c = new nb_ctx();
+    c->device = device;
+    c->n_max = n_max;
+    for (int m = 0; m < 3; m++) c->cfg[m] = default_cfg(m);
+    int rc = NB_OK;
+    auto alloc = [&](void **p, size_t bytes) {
+        if (rc != NB_OK) return;
+        if (cudaMalloc(p, bytes) != cudaSuccess) { cudaGetLastError(); rc = NB_ERR_NOMEM; }
+    };
+    const size_t n = static_cast<size_t>(n_max);
+    alloc(reinterpret_cast<void **>(&c->pos64), n * sizeof(double4_32a));
+    alloc(reinterpret_cast<void **>(&c->vel64), n * sizeof(double4_32a));
+    alloc(reinterpret_cast<void **>(&c->mx_hi), n * sizeof(float4));
+    alloc(reinterpret_cast<void **>(&c->mx_lo), n * sizeof(float4));
+    alloc(reinterpret_cast<void **>(&c->mv_hi), n * sizeof(float4));
+    alloc(reinterpret_cast<void **>(&c->mv_lo), n * sizeof(float4));
+    alloc(reinterpret_cast<void **>(&c->pos32), n * sizeof(float4));
+    alloc(reinterpret_cast<void **>(&c->vel32), n * sizeof(float4));
+    alloc(reinterpret_cast<void **>(&c->d_status), sizeof(int));
+    if (rc == NB_OK && cudaMemset(c->d_status, 0, sizeof(int)) != cudaSuccess) rc = NB_ERR_CUDA;
+    if (rc == NB_OK && cudaDeviceGetAttribute(&c->sm_count, cudaDevAttrMultiProcessorCount, device) != cudaSuccess)
+        rc = NB_ERR_CUDA;
+    if (rc != NB_OK) {
+        nb_destroy(c);
+        return rc;
+    }
+    *out = c;
+    return NB_OK;
+}
+
+void nb_destroy(nb_ctx *c)
+{
+    if (!c) return;
+    DeviceGuard guard(c->device);
+    cudaDeviceSynchronize();
+    void *bufs[] = {c->pos64, c->vel64, c->mx_hi, c->mx_lo, c->mv_hi, c->mv_lo, c->pos32, c->vel32,
+                    c->d_status, c->scratch, c->stage};
+    for (void *b : bufs)
+        if (b) cudaFree(b);
+    delete c;
+}
+
+int nb_sm_count(nb_ctx *ctx) { return ctx ? ctx->sm_count : 0; }
+
+static int predict_impl(nb_ctx *ctx, int64_t offset, int64_t n, const double *x0, const double *v0,
+                        const double *a0, const double *adot0, const double *m, const double *t0,
+                        double t, int forms, cudaStream_t st)
+{
+    if (!ctx) return NB_ERR_ARG;
+    if (offset < 0 || n < 0 || offset + n > ctx->n_max) { ctx->err = "slots outside the context"; return NB_ERR_ARG; }
+    if (n > 0 && (!x0 || !v0 || !m || (a0 && (!adot0 || !t0)))) { ctx->err = "NULL array"; return NB_ERR_ARG; }
+    if (forms == 0) forms = NB_FORM_ALL;
+    if (forms & ~NB_FORM_ALL) { ctx->err = "bad forms mask"; return NB_ERR_ARG; }
+    DeviceGuard guard(ctx->device);
+    nb::PredParams p{};
+    p.offset = offset;
+    p.n = n;
+    p.x0 = x0; p.v0 = v0; p.a0 = a0; p.adot0 = adot0; p.m = m; p.t0 = t0; p.t = t;
+    p.forms = forms;
+    p.pos64 = ctx->pos64; p.vel64 = ctx->vel64;
+    p.mx_hi = ctx->mx_hi; p.mx_lo = ctx->mx_lo; p.mv_hi = ctx->mv_hi; p.mv_lo = ctx->mv_lo;
+    p.pos32 = ctx->pos32; p.vel32 = ctx->vel32;
+    nb::launch_predict(p, st);
+    NB_CUDA(ctx, cudaGetLastError());
+    ctx->forms_valid = forms;   // forms not rewritten are stale now
+    return NB_OK;
+}
+
+int nb_predict(nb_ctx *ctx, int64_t offset, int64_t n, const double *x0, const double *v0,
+               const double *a0, const double *adot0, const double *m, const double *t0, double t,
+               int forms, nb_stream_t stream)
+{
+    if (n > 0 && (!a0 || !adot0 || !t0)) { if (ctx) ctx->err = "NULL array"; return NB_ERR_ARG; }
+    return predict_impl(ctx, offset, n, x0, v0, a0, adot0, m, t0, t, forms,
+                        static_cast<cudaStream_t>(stream));
+}
+
+int nb_set_predicted(nb_ctx *ctx, int64_t offset, int64_t n, const double *x, const double *v,
+                     const double *m, int forms, nb_stream_t stream)
+{
+    return predict_impl(ctx, offset, n, x, v, nullptr, nullptr, m, nullptr, 0.0, forms,
+                        static_cast<cudaStream_t>(stream));
+}
+
+int nb_get_predicted(nb_ctx *ctx, int64_t offset, int64_t n, double *x, double *v, double *m,
+                     nb_stream_t stream)
+{
+    if (!ctx) return NB_ERR_ARG;
+    if (offset < 0 || n < 0 || offset + n > ctx->n_max || (n > 0 && (!x || !v))) {
+        ctx->err = "bad read-back range or NULL array";
+        return NB_ERR_ARG;
+    }
+    if (!(ctx->forms_valid & NB_FORM_FP64)) { ctx->err = "FP64 form not predicted"; return NB_ERR_STATE; }
+    if (n == 0) return NB_OK;
+    DeviceGuard guard(ctx->device);
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    const size_t w = sizeof(double4_32a);
+    const char *p = reinterpret_cast<const char *>(ctx->pos64 + offset);
+    const char *q = reinterpret_cast<const char *>(ctx->vel64 + offset);
+    NB_CUDA(ctx, cudaMemcpy2DAsync(x, 3 * sizeof(double), p, w, 3 * sizeof(double), n, cudaMemcpyDeviceToDevice, st));
+    NB_CUDA(ctx, cudaMemcpy2DAsync(v, 3 * sizeof(double), q, w, 3 * sizeof(double), n, cudaMemcpyDeviceToDevice, st));
+    if (m)
+        NB_CUDA(ctx, cudaMemcpy2DAsync(m, sizeof(double), p + 3 * sizeof(double), w, sizeof(double), n,
+                                       cudaMemcpyDeviceToDevice, st));
+    return NB_OK;
+}
+
+int nb_regular_force(nb_ctx *ctx, int64_t j_begin, int64_t n_j, int32_t n_act, const int32_t *act,
+                     const double *h, const double *dtr, int32_t cap, int mode, double *F, double *J,
+                     double *pot, int32_t *nnb, int32_t *list, uint8_t *ovf, nb_stream_t stream)
+{
+    const Call c{j_begin, n_j, n_act, act, h, dtr, cap, mode, F, J, pot, nnb, list, ovf};
+    return run_single(ctx, c, nullptr, static_cast<cudaStream_t>(stream));
+}
+
+int nb_last_launches(nb_ctx *ctx) { return ctx ? ctx->last_launches : 0; }
+
+int nb_reserve(nb_ctx *ctx, size_t bytes)
+{
+    if (!ctx) return NB_ERR_ARG;
+    DeviceGuard guard(ctx->device);
+    return grow_scratch(ctx, bytes, nullptr);
+}
+
+size_t nb_scratch_bytes(nb_ctx *ctx, int64_t n_j, int32_t n_act, int32_t cap, int mode)
+{
+    if (!ctx || mode < 0 || mode > 2 || n_act <= 0 || n_j <= 0 || cap < 0) return 0;
+    const nb_kcfg cfg = ctx->cfg_set[mode] ? ctx->cfg[mode] : default_cfg(mode);
+    size_t best = 0;
+    for (int flags = 0; flags < 4; flags++) {   // the largest over the flag variants
+        const int idx = find_entry(mode, cfg, flags);
+        if (idx < 0) continue;
+        int occ = 0;
+        if (entry_occupancy(ctx, idx, &occ) != NB_OK) continue;
+        ClusterDesc d{};
+        d.n_j = static_cast<int32_t>(n_j);
+        d.n_act = n_act;
+        d.cap = cap;
+        tile_cluster(registry().all[idx], occ, ctx->sm_count, &cfg, d);
+        best = std::max(best, cluster_scratch(d));
+    }
+    return best;
+}
+
+int nb_sync_status(nb_ctx *ctx, nb_stream_t stream)
+{
+    if (!ctx) return NB_ERR_ARG;
+    DeviceGuard guard(ctx->device);
+    NB_CUDA(ctx, cudaStreamSynchronize(static_cast<cudaStream_t>(stream)));
+    int h = 0;
+    NB_CUDA(ctx, cudaMemcpy(&h, ctx->d_status, sizeof(int), cudaMemcpyDeviceToHost));
+    if (h != 0) NB_CUDA(ctx, cudaMemset(ctx->d_status, 0, sizeof(int)));
+    if (h & nb::DEV_TIMEOUT) { ctx->err = "a bounded copy wait ran out on the device"; return NB_ERR_TIMEOUT; }
+    if (h & nb::DEV_BAD_INPUT) { ctx->err = "invalid active index or radius on the device"; return NB_ERR_DEVICE_INPUT; }
+    return NB_OK;
+}
+
+int nb_num_kernel_configs(int mode)
+{
+    int n = 0;
+    for (const auto &e : registry().all)
+        if (e.mode == mode && e.flags == 0) n++;
+    return n;
+}
+
+int nb_get_kernel_config(int mode, int index, nb_kcfg *out)
+{
+    if (!out) return NB_ERR_ARG;
+    int n = 0;
+    for (const auto &e : registry().all)
+        if (e.mode == mode && e.flags == 0) {
+            if (n == index) { *out = nb_kcfg{e.warps, e.ipw, e.jtile, 0}; return NB_OK; }
+            n++;
+        }
+    return NB_ERR_ARG;
+}
+
+int nb_set_kernel_config(nb_ctx *ctx, int mode, const nb_kcfg *cfg)
+{
+    if (!ctx || mode < 0 || mode > 2) return NB_ERR_ARG;
+    if (!cfg) { ctx->cfg_set[mode] = false; ctx->cfg[mode] = default_cfg(mode); return NB_OK; }
+    if (cfg->split < 0) return NB_ERR_ARG;
+    for (const auto &e : registry().all)
+        if (e.mode == mode && e.flags == 0 && e.warps == cfg->warps && e.ipw == cfg->ipw &&
+            e.jtile == cfg->jtile) {
+            ctx->cfg[mode] = *cfg;
+            ctx->cfg_set[mode] = true;
+            return NB_OK;
+        }
+    return NB_ERR_UNSUPPORTED;
+}
+
+int nb_get_active_config(nb_ctx *ctx, int mode, nb_kcfg *out)
+{
+    if (!ctx || !out || mode < 0 || mode > 2) return NB_ERR_ARG;
+    *out = ctx->cfg_set[mode] ? ctx->cfg[mode] : default_cfg(mode);
+    return NB_OK;
+}
+
+int nb_time_regular_force(nb_ctx *ctx, const nb_kcfg *cfg, int64_t j_begin, int64_t n_j,
+                          int32_t n_act, const int32_t *act, const double *h, const double *dtr,
+                          int32_t cap, int mode, double *F, double *J, double *pot, int32_t *nnb,
+                          int32_t *list, uint8_t *ovf, int reps, nb_stream_t stream, float *ms)
+{
+    if (!ctx || !cfg || !ms || reps <= 0) return NB_ERR_ARG;
+    DeviceGuard guard(ctx->device);
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    const Call c{j_begin, n_j, n_act, act, h, dtr, cap, mode, F, J, pot, nnb, list, ovf};
+    int rc = run_single(ctx, c, cfg, st);   // warm-up (and scratch growth)
+    if (rc != NB_OK) return rc;
+    cudaEvent_t a, b;
+    NB_CUDA(ctx, cudaEventCreate(&a));
+    NB_CUDA(ctx, cudaEventCreate(&b));
+    cudaEventRecord(a, st);
+    for (int r = 0; r < reps && rc == NB_OK; r++) rc = run_single(ctx, c, cfg, st);
+    cudaEventRecord(b, st);
+    cudaError_t e = cudaEventSynchronize(b);
+    float t = 0.f;
+    if (e == cudaSuccess) e = cudaEventElapsedTime(&t, a, b);
+    cudaEventDestroy(a);
+    cudaEventDestroy(b);
+    if (rc != NB_OK) return rc;
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "timing events");
+    *ms = t / reps;
+    return NB_OK;
+}
+
+// ------------------------------------------------------------ host step
+
+int nb_step_host(nb_ctx *ctx, int64_t n, const double *x0, const double *v0, const double *a0,
+                 const double *adot0, const double *m, const double *t0, double t, int32_t n_act,
+                 const int32_t *act, const double *h, const double *dtr, int32_t cap, int mode,
+                 double *F, double *J, double *pot, int32_t *nnb, int32_t *list, uint8_t *ovf,
+                 nb_stream_t stream)
+{
+    if (!ctx) return NB_ERR_ARG;
+    if (n <= 0 || n > ctx->n_max || n_act < 0 || cap < 0 || mode < 0 || mode > 2) {
+        ctx->err = "bad sizes";
+        return NB_ERR_ARG;
+    }
+    if (!x0 || !v0 || !a0 || !adot0 || !m || !t0) { ctx->err = "NULL host input"; return NB_ERR_ARG; }
+    if (n_act > 0 && (!act || !h || !F || !J || !nnb || !ovf || (cap > 0 && !list))) {
+        ctx->err = "NULL host array";
+        return NB_ERR_ARG;
+    }
+    DeviceGuard guard(ctx->device);
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    const size_t nn = static_cast<size_t>(n), na = static_cast<size_t>(n_act);
+    size_t off = 0;
+    auto take = [&](size_t bytes) { size_t o = off; off = align_up(off + bytes, 256); return o; };
+    const size_t o_in = take(nn * 14 * sizeof(double));
+    const size_t o_act = take(na * sizeof(int32_t));
+    const size_t o_h = take(na * sizeof(double));
+    const size_t o_dtr = take(dtr ? na * sizeof(double) : 0);
+    const size_t o_F = take(na * 3 * sizeof(double));
+    const size_t o_J = take(na * 3 * sizeof(double));
+    const size_t o_pot = take(pot ? na * sizeof(double) : 0);
+    const size_t o_nnb = take(na * sizeof(int32_t));
+    const size_t o_list = take(na * static_cast<size_t>(cap) * sizeof(int32_t));
+    const size_t o_ovf = take(na);
+    if (off > ctx->stage_bytes) {
+        NB_CUDA(ctx, cudaStreamSynchronize(st));
+        if (ctx->stage) cudaFree(ctx->stage);
+        ctx->stage = nullptr;
+        ctx->stage_bytes = 0;
+        if (cudaMalloc(&ctx->stage, off) != cudaSuccess) {
+            cudaGetLastError();
+            ctx->err = "cannot allocate host-step staging";
+            return NB_ERR_NOMEM;
+        }
+        ctx->stage_bytes = off;
+    }
+    char *s = static_cast<char *>(ctx->stage);
+    double *d_in = reinterpret_cast<double *>(s + o_in);
+    const size_t v3 = nn * 3 * sizeof(double);
+    NB_CUDA(ctx, cudaMemcpyAsync(d_in, x0, v3, cudaMemcpyHostToDevice, st));
+    NB_CUDA(ctx, cudaMemcpyAsync(d_in + 3 * nn, v0, v3, cudaMemcpyHostToDevice, st));
+    NB_CUDA(ctx, cudaMemcpyAsync(d_in + 6 * nn, a0, v3, cudaMemcpyHostToDevice, st));
+    NB_CUDA(ctx, cudaMemcpyAsync(d_in + 9 * nn, adot0, v3, cudaMemcpyHostToDevice, st));
+    NB_CUDA(ctx, cudaMemcpyAsync(d_in + 12 * nn, m, nn * sizeof(double), cudaMemcpyHostToDevice, st));
+    NB_CUDA(ctx, cudaMemcpyAsync(d_in + 13 * nn, t0, nn * sizeof(double), cudaMemcpyHostToDevice, st));
+    if (n_act > 0) {
+        NB_CUDA(ctx, cudaMemcpyAsync(s + o_act, act, na * sizeof(int32_t), cudaMemcpyHostToDevice, st));
+        NB_CUDA(ctx, cudaMemcpyAsync(s + o_h, h, na * sizeof(double), cudaMemcpyHostToDevice, st));
+        if (dtr) NB_CUDA(ctx, cudaMemcpyAsync(s + o_dtr, dtr, na * sizeof(double), cudaMemcpyHostToDevice, st));
+    }
+    int rc = nb_predict(ctx, 0, n, d_in, d_in + 3 * nn, d_in + 6 * nn, d_in + 9 * nn, d_in + 12 * nn,
+                        d_in + 13 * nn, t, mode_forms(mode), st);
+    if (rc != NB_OK) return rc;
+    int launches = 1;
+    if (n_act > 0) {
+        rc = nb_regular_force(ctx, 0, n, n_act, reinterpret_cast<int32_t *>(s + o_act),
+                              reinterpret_cast<double *>(s + o_h),
+                              dtr ? reinterpret_cast<double *>(s + o_dtr) : nullptr, cap, mode,
+                              reinterpret_cast<double *>(s + o_F), reinterpret_cast<double *>(s + o_J),
+                              pot ? reinterpret_cast<double *>(s + o_pot) : nullptr,
+                              reinterpret_cast<int32_t *>(s + o_nnb),
+                              cap > 0 ? reinterpret_cast<int32_t *>(s + o_list) : nullptr,
+                              reinterpret_cast<uint8_t *>(s + o_ovf), st);
+        if (rc != NB_OK) return rc;
+        launches += ctx->last_launches;
+        NB_CUDA(ctx, cudaMemcpyAsync(F, s + o_F, na * 3 * sizeof(double), cudaMemcpyDeviceToHost, st));
+        NB_CUDA(ctx, cudaMemcpyAsync(J, s + o_J, na * 3 * sizeof(double), cudaMemcpyDeviceToHost, st));
+        if (pot) NB_CUDA(ctx, cudaMemcpyAsync(pot, s + o_pot, na * sizeof(double), cudaMemcpyDeviceToHost, st));
+        NB_CUDA(ctx, cudaMemcpyAsync(nnb, s + o_nnb, na * sizeof(int32_t), cudaMemcpyDeviceToHost, st));
+        if (cap > 0)
+            NB_CUDA(ctx, cudaMemcpyAsync(list, s + o_list, na * static_cast<size_t>(cap) * sizeof(int32_t),
+                                         cudaMemcpyDeviceToHost, st));
+        NB_CUDA(ctx, cudaMemcpyAsync(ovf, s + o_ovf, na, cudaMemcpyDeviceToHost, st));
+    }
+    rc = nb_sync_status(ctx, stream);
+    ctx->last_launches = launches;
+    return rc;
+}
+
+// --------------------------------------------------------------- plans
+
+void nb_plan_destroy(nb_plan *p)
+{
+    if (!p) return;
+    DeviceGuard guard(p->ctx->device);
+    if (p->exec) cudaGraphExecDestroy(p->exec);
+    if (p->graph) cudaGraphDestroy(p->graph);
+    void *bufs[] = {p->d_table, p->d_item_begin, p->d_act_begin, p->d_cluster_of, p->scratch};
+    for (void *b : bufs)
+        if (b) cudaFree(b);
+    delete p;
+}
+
+int nb_plan_create(nb_ctx *ctx, int32_t n_clusters, const nb_cluster *cl, int mode,
+                   const nb_kcfg *cfg_in, nb_plan **out)
+{
+    if (!ctx || !out || n_clusters <= 0 || !cl) return NB_ERR_ARG;
+    *out = nullptr;
+    DeviceGuard guard(ctx->device);
+    int flags = 0;
+    for (int c = 0; c < n_clusters; c++) {
+        const Call call{cl[c].j_begin, cl[c].n_j, cl[c].n_act, cl[c].act, cl[c].h, cl[c].dtr, cl[c].cap,
+                        mode, cl[c].F, cl[c].J, cl[c].pot, cl[c].nnb, cl[c].list, cl[c].ovf};
+        const int rc = check_call(ctx, call);
+        if (rc != NB_OK) return rc;
+        flags |= (cl[c].dtr ? 1 : 0) | (cl[c].pot ? 2 : 0);
+    }
+    const nb_kcfg cfg = cfg_in ? *cfg_in : (ctx->cfg_set[mode] ? ctx->cfg[mode] : default_cfg(mode));
+    const int idx = find_entry(mode, cfg, flags);
+    if (idx < 0) return NB_ERR_UNSUPPORTED;
+    int occ = 0;
+    int rc = entry_occupancy(ctx, idx, &occ);
+    if (rc != NB_OK) return rc;
+    nb_plan *p = new nb_plan();
+    p->ctx = ctx;
+    p->mode = mode;
+    p->entry = idx;
+    p->e = &registry().all[idx];
+    // Tile every cluster.  Splits are chosen for the whole batch: the number
+    // of work items across clusters should cover the resident CTA slots.
+    std::vector<ClusterDesc> &ds = p->descs;
+    int64_t iblk_total = 0;
+    for (int c = 0; c < n_clusters; c++) {
+        const Call call{cl[c].j_begin, cl[c].n_j, cl[c].n_act, cl[c].act, cl[c].h, cl[c].dtr, cl[c].cap,
+                        mode, cl[c].F, cl[c].J, cl[c].pot, cl[c].nnb, cl[c].list, cl[c].ovf};
+        ds.push_back(make_desc(call));
+        ClusterDesc &d = ds.back();
+        const int ipb = p->e->warps * p->e->ipw;
+        d.n_iblk = (d.n_act + ipb - 1) / ipb;
+        iblk_total += d.n_iblk;
+    }
+    // a common target length of a j-split (in tiles) for the batch
+    int64_t work_tiles = 0;
+    for (auto &d : ds) work_tiles += static_cast<int64_t>(d.n_iblk) * ((d.n_j + p->e->jtile - 1) / p->e->jtile);
+    const int64_t slots = static_cast<int64_t>(ctx->sm_count) * occ;
+    int tps = cfg.split > 0 ? cfg.split
+                            : static_cast<int>(std::max<int64_t>(2, work_tiles / std::max<int64_t>(1, 8 * slots)));
+    size_t scratch = 0;
+    int64_t items = 0;
+    for (auto &d : ds) {
+        nb_kcfg fixed = cfg;
+        fixed.split = tps;
+        tile_cluster(*p->e, occ, ctx->sm_count, &fixed, d);
+        d.item_begin = items;
+        items += static_cast<int64_t>(d.n_iblk) * d.n_split;
+        scratch += cluster_scratch(d);
+    }
+    p->n_items = items;
+    p->grid = static_cast<int>(std::min<int64_t>(std::max<int64_t>(items, 1), slots));
+    auto fail = [&](int code) { nb_plan_destroy(p); return code; };
+    if (scratch > 0) {
+        if (cudaMalloc(&p->scratch, scratch) != cudaSuccess) { cudaGetLastError(); return fail(NB_ERR_NOMEM); }
+    }
+    char *base = static_cast<char *>(p->scratch);
+    std::vector<int64_t> item_begin, act_begin;
+    std::vector<int32_t> cluster_of;
+    int64_t merged = 0;
+    for (int c = 0; c < n_clusters; c++) {
+        ClusterDesc &d = ds[c];
+        carve_scratch(d, base);
+        base += cluster_scratch(d);
+        item_begin.push_back(d.item_begin);
+        if (d.n_split > 1 && d.n_act > 0) {
+            act_begin.push_back(merged);
+            cluster_of.push_back(c);
+            merged += d.n_act;
+        }
+    }
+    p->n_merge = static_cast<int>(cluster_of.size());
+    p->merge_total = merged;
+    if (cudaMalloc(&p->d_table, ds.size() * sizeof(ClusterDesc)) != cudaSuccess ||
+        cudaMalloc(&p->d_item_begin, item_begin.size() * sizeof(int64_t)) != cudaSuccess) {
+        cudaGetLastError();
+        return fail(NB_ERR_NOMEM);
+    }
+    if (cudaMemcpy(p->d_table, ds.data(), ds.size() * sizeof(ClusterDesc), cudaMemcpyHostToDevice) != cudaSuccess ||
+        cudaMemcpy(p->d_item_begin, item_begin.data(), item_begin.size() * sizeof(int64_t),
+                   cudaMemcpyHostToDevice) != cudaSuccess)
+        return fail(NB_ERR_CUDA);
+    if (p->n_merge > 0) {
+        if (cudaMalloc(&p->d_act_begin, act_begin.size() * sizeof(int64_t)) != cudaSuccess ||
+            cudaMalloc(&p->d_cluster_of, cluster_of.size() * sizeof(int32_t)) != cudaSuccess) {
+            cudaGetLastError();
+            return fail(NB_ERR_NOMEM);
+        }
+        if (cudaMemcpy(p->d_act_begin, act_begin.data(), act_begin.size() * sizeof(int64_t),
+                       cudaMemcpyHostToDevice) != cudaSuccess ||
+            cudaMemcpy(p->d_cluster_of, cluster_of.data(), cluster_of.size() * sizeof(int32_t),
+                       cudaMemcpyHostToDevice) != cudaSuccess)
+            return fail(NB_ERR_CUDA);
+    }
+    *out = p;
+    return NB_OK;
+}
+
+int nb_plan_launches(const nb_plan *p) { return p ? (p->n_items > 0 ? 1 : 0) + (p->n_merge > 0 ? 1 : 0) : 0; }
+
+int nb_plan_run(nb_plan *p, nb_stream_t stream)
+{
+    if (!p) return NB_ERR_ARG;
+    nb_ctx *ctx = p->ctx;
+    if (!(ctx->forms_valid & mode_forms(p->mode))) { ctx->err = "form not predicted"; return NB_ERR_STATE; }
+    DeviceGuard guard(ctx->device);
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    if (p->n_items > 0) {
+        nb::RegfParams rp{};
+        rp.js = jset(ctx, p->mode);
+        rp.table = p->d_table;
+        rp.item_begin = p->d_item_begin;
+        rp.n_clusters = static_cast<int32_t>(p->descs.size());
+        rp.n_items = p->n_items;
+        rp.status = ctx->d_status;
+        rp.wait_ns = ctx->wait_ns;
+        rp.extra_tx = ctx->extra_tx;
+        void *args[] = {&rp};
+        NB_CUDA(ctx, cudaLaunchKernel(p->e->fn, dim3(p->grid), dim3(p->e->warps * 32), args, p->e->smem, st));
+    }
+    if (p->n_merge > 0) {
+        nb::MergeParams mp{};
+        mp.table = p->d_table;
+        mp.act_begin = p->d_act_begin;
+        mp.cluster_of = p->d_cluster_of;
+        mp.n_clusters = p->n_merge;
+        mp.n_total = p->merge_total;
+        nb::launch_merge(mp, st);
+        NB_CUDA(ctx, cudaGetLastError());
+    }
+    return NB_OK;
+}
+
+int nb_plan_capture(nb_plan *p, nb_stream_t stream)
+{
+    if (!p) return NB_ERR_ARG;
+    nb_ctx *ctx = p->ctx;
+    DeviceGuard guard(ctx->device);
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    if (p->exec) { cudaGraphExecDestroy(p->exec); p->exec = nullptr; }
+    if (p->graph) { cudaGraphDestroy(p->graph); p->graph = nullptr; }
+    NB_CUDA(ctx, cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal));
+    const int rc = nb_plan_run(p, stream);
+    cudaGraph_t g = nullptr;
+    const cudaError_t e = cudaStreamEndCapture(st, &g);
+    if (rc != NB_OK) { if (g) cudaGraphDestroy(g); return rc; }
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "cudaStreamEndCapture");
+    p->graph = g;
+    NB_CUDA(ctx, cudaGraphInstantiate(&p->exec, g, 0));
+    return NB_OK;
+}
+
+int nb_plan_launch(nb_plan *p, nb_stream_t stream)
+{
+    if (!p) return NB_ERR_ARG;
+    if (!p->exec) { p->ctx->err = "plan has no captured graph"; return NB_ERR_STATE; }
+    DeviceGuard guard(p->ctx->device);
+    NB_CUDA(p->ctx, cudaGraphLaunch(p->exec, static_cast<cudaStream_t>(stream)));
+    return NB_OK;
+}
+
+// Test hooks (not in the public header): bound of every device copy wait and
+// extra transaction bytes that make every wait run out.
+int nb_debug_set_wait(nb_ctx *ctx, uint64_t wait_ns, uint32_t extra_tx)
+{
+    if (!ctx) return NB_ERR_ARG;
+    ctx->wait_ns = wait_ns ? wait_ns : kDefaultWaitNs;
+    ctx->extra_tx = extra_tx & ~15u;
+    return NB_OK;
+}
+
+}  // extern "C"

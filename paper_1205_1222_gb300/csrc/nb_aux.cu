@@ -1,0 +1,140 @@
+// Predictor and split-merge kernels of libnbreg.
+//
+//  * predict_kernel: advances every j-particle to the block time with the
+//    third-order Taylor polynomial in a, da/dt (Sec. 3.3 step (iii); the
+//    paper does this on the host before GPUNB_SEND) and writes the stored
+//    copies the force kernels read: FP64 double4 (x,y,z,m) + (vx,vy,vz,0),
+//    two-float float4 hi/lo pairs of position and velocity (mass in the
+//    hi-position w), and plain FP32 float4 copies.
+//  * merge_kernel: one warp per active particle of a cluster whose j-range
+//    was split over several work items; sums the per-split FP64 partial
+//    force, jerk and potential in a fixed order and concatenates the
+//    per-split partial lists in split order (ascending j), keeping the first
+//    `cap` entries (Sec. 3.4: force reduction and list gathering kernels).
+#include <cstdint>
+
+#include "nb_aux.cuh"
+
+namespace nb {
+
+__global__ void predict_kernel(const PredParams p)
+{
+    const int64_t j = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
+    if (j >= p.n) return;
+    double x[3], v[3];
+    const double m = p.m[j];
+    if (p.a0) {
+        const double dt = p.t - p.t0[j];
+        for (int k = 0; k < 3; k++) {
+            const double x0 = p.x0[3 * j + k], v0 = p.v0[3 * j + k];
+            const double a = p.a0[3 * j + k], ad = p.adot0[3 * j + k];
+            // Horner form of x0 + v0 dt + a dt^2/2 + ad dt^3/6 and v0 + a dt + ad dt^2/2
+            x[k] = fma(dt, fma(dt, fma(dt, ad * (1.0 / 6.0), a * 0.5), v0), x0);
+            v[k] = fma(dt, fma(dt, ad * 0.5, a), v0);
+        }
+    } else {
+        for (int k = 0; k < 3; k++) { x[k] = p.x0[3 * j + k]; v[k] = p.v0[3 * j + k]; }
+    }
+    const int64_t s = p.offset + j;
+    if (p.forms & 1) {
+        p.pos64[s] = make_double4_32a(x[0], x[1], x[2], m);
+        p.vel64[s] = make_double4_32a(v[0], v[1], v[2], 0.0);
+    }
+    if (p.forms & 2) {
+        float xh[3], xl[3], vh[3], vl[3];
+        for (int k = 0; k < 3; k++) {
+            xh[k] = __double2float_rn(x[k]);
+            xl[k] = __double2float_rn(x[k] - static_cast<double>(xh[k]));
+            vh[k] = __double2float_rn(v[k]);
+            vl[k] = __double2float_rn(v[k] - static_cast<double>(vh[k]));
+        }
+        p.mx_hi[s] = make_float4(xh[0], xh[1], xh[2], __double2float_rn(m));
+        p.mx_lo[s] = make_float4(xl[0], xl[1], xl[2], 0.f);
+        p.mv_hi[s] = make_float4(vh[0], vh[1], vh[2], 0.f);
+        p.mv_lo[s] = make_float4(vl[0], vl[1], vl[2], 0.f);
+    }
+    if (p.forms & 4) {
+        p.pos32[s] = make_float4(__double2float_rn(x[0]), __double2float_rn(x[1]),
+                                 __double2float_rn(x[2]), __double2float_rn(m));
+        p.vel32[s] = make_float4(__double2float_rn(v[0]), __double2float_rn(v[1]),
+                                 __double2float_rn(v[2]), 0.f);
+    }
+}
+
+__global__ void merge_kernel(const MergeParams p)
+{
+    const int64_t w = (static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
+    if (w >= p.n_total) return;
+    ClusterDesc d;
+    int64_t i;
+    if (p.table) {
+        int lo = 0, hi = p.n_clusters - 1;
+        while (lo < hi) {
+            const int mid = (lo + hi + 1) >> 1;
+            if (p.act_begin[mid] <= w) lo = mid; else hi = mid - 1;
+        }
+        d = p.table[p.cluster_of[lo]];
+        i = w - p.act_begin[lo];
+    } else {
+        d = p.d0;
+        i = w;
+    }
+    const int S = d.n_split;
+    const int64_t na = d.n_act;
+    double sum[7] = {0, 0, 0, 0, 0, 0, 0};
+    int running = 0;
+    for (int s0 = 0; s0 < S; s0 += 32) {
+        const int s = s0 + lane;
+        int c = 0;
+        if (s < S) {
+            c = d.pcnt[s * na + i];
+            const double *q = d.pF + (s * na + i) * 8;
+            for (int k = 0; k < 7; k++) sum[k] += q[k];
+        }
+        int incl = c;
+        for (int o = 1; o < 32; o <<= 1) {
+            const int t = __shfl_up_sync(0xffffffffu, incl, o);
+            if (lane >= o) incl += t;
+        }
+        const int base = running + incl - c;
+        unsigned todo = __ballot_sync(0xffffffffu, c > 0 && base < d.cap);
+        while (todo) {
+            const int src = __ffs(todo) - 1;
+            todo &= todo - 1;
+            const int sc = __shfl_sync(0xffffffffu, c, src);
+            const int sb = __shfl_sync(0xffffffffu, base, src);
+            const int ncopy = min(sc, d.cap - sb);
+            const int32_t *from = d.plist + (static_cast<int64_t>(s0 + src) * na + i) * d.cap;
+            int32_t *to = d.list + i * d.cap + sb;
+            for (int e = lane; e < ncopy; e += 32) to[e] = from[e];
+        }
+        running += __shfl_sync(0xffffffffu, incl, 31);
+    }
+    for (int o = 16; o > 0; o >>= 1)
+        for (int k = 0; k < 7; k++) sum[k] += __shfl_xor_sync(0xffffffffu, sum[k], o);
+    if (lane == 0) {
+        for (int k = 0; k < 3; k++) { d.F[3 * i + k] = sum[k]; d.J[3 * i + k] = sum[3 + k]; }
+        if (d.pot) d.pot[i] = sum[6];
+        d.nnb[i] = running;
+        d.ovf[i] = running > d.cap ? 1 : 0;
+    }
+}
+
+void launch_predict(const PredParams &p, cudaStream_t st)
+{
+    if (p.n <= 0) return;
+    const int threads = 256;
+    const int64_t blocks = (p.n + threads - 1) / threads;
+    predict_kernel<<<static_cast<unsigned>(blocks), threads, 0, st>>>(p);
+}
+
+void launch_merge(const MergeParams &p, cudaStream_t st)
+{
+    if (p.n_total <= 0) return;
+    const int threads = 256;
+    const int64_t blocks = (p.n_total * 32 + threads - 1) / threads;
+    merge_kernel<<<static_cast<unsigned>(blocks), threads, 0, st>>>(p);
+}
+
+}  // namespace nb

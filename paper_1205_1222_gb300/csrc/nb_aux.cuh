@@ -1,0 +1,47 @@
+// Host-visible declarations of the predictor / merge kernels and of the
+// regular-force kernel registry.
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#include "nb_device.cuh"
+
+namespace nb {
+
+struct PredParams {
+    int64_t offset, n;
+    const double *x0, *v0, *a0, *adot0, *m, *t0;   // a0 == nullptr: copy x0, v0 unchanged
+    double t;
+    int forms;
+    double4_32a *pos64, *vel64;
+    float4 *mx_hi, *mx_lo, *mv_hi, *mv_lo;
+    float4 *pos32, *vel32;
+};
+
+struct MergeParams {
+    ClusterDesc d0;                // single cluster (table == nullptr)
+    const ClusterDesc *table;      // cluster table of a batched plan
+    const int64_t *act_begin;      // [n_clusters] prefix of n_act over the merged clusters
+    const int32_t *cluster_of;     // [n_clusters] index into table of each merged cluster
+    int32_t n_clusters;            // merged clusters
+    int64_t n_total;               // total merged active particles (one warp each)
+};
+
+void launch_predict(const PredParams &p, cudaStream_t st);
+void launch_merge(const MergeParams &p, cudaStream_t st);
+
+// One compiled instantiation of the regular-force kernel.
+struct KernelEntry {
+    int mode;        // 0 FP64, 1 MIXED, 2 FP32
+    int warps, ipw, jtile;
+    int flags;       // bit 0: velocity criterion, bit 1: potential
+    const void *fn;
+    int smem;        // dynamic shared memory bytes
+};
+
+const KernelEntry *kernels_fp64(int *count);
+const KernelEntry *kernels_mixed(int *count);
+const KernelEntry *kernels_fp32(int *count);
+
+}  // namespace nb

@@ -1,0 +1,160 @@
+// Device-side definitions shared by the kernels of libnbreg: work-item
+// descriptors, the asynchronous-copy (TMA bulk) and mbarrier primitives, the
+// float-float helpers and the device status bits.
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace nb {
+
+// Device status bits (OR-ed into the context's status word).
+enum : int {
+    DEV_TIMEOUT = 1,    // a bounded wait on a copy ran out
+    DEV_BAD_INPUT = 2,  // an active index or a radius was invalid
+};
+
+// Predicted j-set of one precision form: base pointers of its streams.
+struct JSet {
+    const void *s[4];
+};
+
+// One cluster of a regular-force launch, as the kernels see it.
+struct ClusterDesc {
+    int64_t j_begin;       // first slot of the cluster in the predicted set
+    int32_t n_j;           // j-particles
+    int32_t n_act;         // active particles
+    int32_t cap;           // list capacity
+    int32_t n_split;       // j-splits (work items per i-block)
+    int32_t tiles_per_split;
+    int32_t n_tiles;       // ceil(n_j / jtile)
+    int32_t n_iblk;        // ceil(n_act / (warps * ipw))
+    int32_t pad0;
+    int64_t item_begin;    // first work item of this cluster
+    const int32_t *act;
+    const double *h;
+    const double *dtr;
+    double *F, *J, *pot;
+    int32_t *nnb;
+    int32_t *list;
+    uint8_t *ovf;
+    // split scratch (n_split > 1): 8 doubles (F3, J3, pot, -) per (split, i),
+    // a count per (split, i) and `cap` list slots per (split, i)
+    double *pF;
+    int32_t *pcnt;
+    int32_t *plist;
+};
+
+struct RegfParams {
+    JSet js;
+    ClusterDesc d0;               // used when table == nullptr
+    const ClusterDesc *table;     // device table of clusters (batched launch)
+    const int64_t *item_begin;    // [n_clusters] copy of table[c].item_begin for the search
+    int32_t n_clusters;
+    int64_t n_items;
+    int *status;
+    uint64_t wait_ns;             // bound of every mbarrier wait
+    uint32_t extra_tx;            // test hook: bytes expected beyond the copies (0 normally);
+                                  // > 0 makes every copy wait run out, exercising the time-out path
+};
+
+// ------------------------------------------------------------ PTX helpers
+
+__device__ __forceinline__ uint32_t smem_u32(const void *p)
+{
+    return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+
+__device__ __forceinline__ void mbar_init(uint64_t *bar, uint32_t count)
+{
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count)
+                 : "memory");
+}
+
+__device__ __forceinline__ void fence_mbar_init()
+{
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t *bar, uint32_t bytes)
+{
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)),
+                 "r"(bytes)
+                 : "memory");
+}
+
+// Bulk asynchronous copy global -> shared (the untiled TMA path), completing
+// `bytes` transactions on `bar`.  dst, src 16-byte aligned, bytes % 16 == 0.
+__device__ __forceinline__ void tma_bulk_g2s(void *dst, const void *src, uint32_t bytes,
+                                             uint64_t *bar)
+{
+    asm volatile(
+        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::
+            "r"(smem_u32(dst)),
+        "l"(src), "r"(bytes), "r"(smem_u32(bar))
+        : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t parity)
+{
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.b32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(smem_u32(bar)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+
+__device__ __forceinline__ uint64_t global_ns()
+{
+    uint64_t t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+// Wait for phase `parity` of `bar`, giving up after `limit_ns` nanoseconds.
+// Returns false on time-out (the caller reports it and stops).
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t *bar, uint32_t parity, uint64_t limit_ns)
+{
+    if (mbar_try_wait(bar, parity)) return true;
+    const uint64_t t0 = global_ns();
+    while (true) {
+        if (mbar_try_wait(bar, parity)) return true;
+        if (global_ns() - t0 > limit_ns) return false;
+    }
+}
+
+// ---------------------------------------------------------- float-float
+
+// hi + lo += p with the rounding error of the high part kept (Knuth's TwoSum).
+__device__ __forceinline__ void ff_add(float &hi, float &lo, float p)
+{
+    const float s = __fadd_rn(hi, p);
+    const float bp = __fsub_rn(s, hi);
+    const float e = __fadd_rn(__fsub_rn(hi, __fsub_rn(s, bp)), __fsub_rn(p, bp));
+    hi = s;
+    lo = __fadd_rn(lo, e);
+}
+
+// (hi, lo) += (h2, l2), result renormalised so that |lo| <= ulp(hi)/2.
+__device__ __forceinline__ void ff_add_ff(float &hi, float &lo, float h2, float l2)
+{
+    const float s = __fadd_rn(hi, h2);
+    const float bp = __fsub_rn(s, hi);
+    float e = __fadd_rn(__fsub_rn(hi, __fsub_rn(s, bp)), __fsub_rn(h2, bp));
+    e = __fadd_rn(e, __fadd_rn(lo, l2));
+    hi = __fadd_rn(s, e);
+    lo = __fsub_rn(e, __fsub_rn(hi, s));
+}
+
+__device__ __forceinline__ unsigned lanemask_lt()
+{
+    unsigned m;
+    asm("mov.u32 %0, %%lanemask_lt;" : "=r"(m));
+    return m;
+}
+
+}  // namespace nb

@@ -1,0 +1,21 @@
+// Compiled configurations of the plain FP32 (NB_FP32) regular-force kernel.
+#include "nb_kernels.cuh"
+
+namespace nb {
+
+static const KernelEntry g_fp32[] = {
+    NB_KERNEL_ENTRY(FormFP32, 2, 8, 4, 512, 0),
+    NB_KERNEL_ENTRY(FormFP32, 2, 8, 4, 512, 1),
+    NB_KERNEL_ENTRY(FormFP32, 2, 8, 4, 512, 2),
+    NB_KERNEL_ENTRY(FormFP32, 2, 8, 4, 512, 3),
+    NB_KERNEL_ENTRY(FormFP32, 2, 8, 8, 512, 0),
+    NB_KERNEL_ENTRY(FormFP32, 2, 8, 2, 512, 0),
+};
+
+const KernelEntry *kernels_fp32(int *count)
+{
+    *count = static_cast<int>(sizeof(g_fp32) / sizeof(g_fp32[0]));
+    return g_fp32;
+}
+
+}  // namespace nb

@@ -1,0 +1,374 @@
+"""Parity of the CUDA path (through the C-ABI) with the FP64 oracle.
+
+Small cases span several j-tiles, ragged tails and every compiled kernel
+configuration; the full-size cases use the launch configuration the benchmark
+times and compare sampled active particles one by one, plus properties that
+hold at any size (every particle's neighbour count equals the count the
+radius was constructed for).
+"""
+import ctypes
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_1205_1222_gb300 import Context, binding as B, build, inputs, mode_id
+from tests.gpu_util import (TOL, compare, dev, direct_sum_accel, gpu_run, list_mismatches, oracle_predicted,
+                            oracle_run, rel_err, upload)
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _lib():
+    build.build()
+    import torch
+    assert torch.cuda.is_available(), "GPU tests need a CUDA device"
+
+
+@pytest.fixture(scope="module")
+def cfg1():
+    return inputs.config1(accel=direct_sum_accel)
+
+
+@pytest.fixture(scope="module")
+def cfg2():
+    return inputs.cached(inputs.config2)
+
+
+# ------------------------------------------------------------ small cases
+
+@pytest.mark.parametrize("mode", ["fp64", "mixed", "fp32"])
+def test_config1_plummer_1024(cfg1, mode):
+    g = gpu_run(cfg1, mode)
+    assert g["status"] == 0
+    o = oracle_run(cfg1)
+    compare(g, o, cfg1.cap, mode, lists=(mode != "fp32"))
+    if mode == "fp32":
+        assert list_mismatches(g, o, cfg1.cap) <= cfg1.n_act // 50
+
+
+def test_predictor_matches_oracle(cfg1):
+    import torch
+    w = cfg1
+    with Context(w.n) as ctx:
+        d = upload(w)
+        ctx.predict(d["x0"], d["v0"], d["a0"], d["adot0"], d["m"], d["t0"], w.t)
+        x = torch.empty((w.n, 3), dtype=torch.float64, device="cuda")
+        v = torch.empty_like(x)
+        m = torch.empty(w.n, dtype=torch.float64, device="cuda")
+        B.nb_get_predicted(ctx.h, 0, w.n, x, v, m)
+        torch.cuda.synchronize()
+        xo, vo = oracle_predicted(w)
+        assert np.max(np.abs(x.cpu().numpy() - xo)) <= 4e-16 * np.max(np.abs(xo)) * 4
+        assert np.max(np.abs(v.cpu().numpy() - vo)) <= 4e-16 * np.max(np.abs(vo)) * 4
+        assert np.array_equal(m.cpu().numpy(), w.m)
+
+
+@pytest.mark.parametrize("n_act", [16, 64, 256, 1024, 4096, 16384])
+@pytest.mark.parametrize("mode", ["fp64", "mixed"])
+def test_config2_block_step_sweep(cfg2, n_act, mode):
+    w = inputs.subset(cfg2, n_act, 2) if n_act < cfg2.n else cfg2
+    g = gpu_run(w, mode)
+    assert g["status"] == 0
+    compare(g, oracle_run(w), w.cap, mode)
+
+
+@pytest.mark.parametrize("n,n_act", [(33, 33), (1000, 31), (1537, 200), (2049, 2049), (4097, 65)])
+@pytest.mark.parametrize("mode", ["fp64", "mixed"])
+def test_ragged_sizes(n, n_act, mode):
+    w = inputs.cluster(n, 100 + n, min(16, n - 2) if n > 3 else 1, 64,
+                       act=np.sort(np.random.default_rng(n).choice(n, n_act, replace=False)))
+    g = gpu_run(w, mode)
+    assert g["status"] == 0
+    compare(g, oracle_run(w), w.cap, mode)
+
+
+def test_two_bodies():
+    """Two particles: each sees the other (h > r) or feels it (h < r)."""
+    import types
+    for h, nnb in ((0.5, 0), (3.0, 1)):
+        w = inputs.cluster(40, 21, 8, 4)
+        w2 = types.SimpleNamespace(**{k: getattr(w, k) for k in ("x0", "v0", "a0", "adot0", "m", "t0", "t")})
+        for k in ("x0", "v0", "a0", "adot0", "m", "t0"):
+            setattr(w2, k, getattr(w, k)[:2].copy())
+        w2.x0[1] = w2.x0[0] + np.array([1.0, 0.5, -0.25])
+        w2.n, w2.n_act, w2.cap, w2.dtr = 2, 2, 4, None
+        w2.act = np.array([0, 1], dtype=np.int32)
+        w2.h = np.array([h, h])
+        for mode in ("fp64", "mixed", "fp32"):
+            g = gpu_run(w2, mode)
+            o = oracle_run(w2)
+            assert np.all(g["nnb"] == nnb)
+            compare(g, o, 4, mode)
+
+
+def test_zero_radius_gives_the_full_sum():
+    w = inputs.cluster(3000, 7, 8, 16)
+    w.h[:] = 0.0
+    for mode in ("fp64", "mixed"):
+        g = gpu_run(w, mode)
+        assert np.all(g["nnb"] == 0) and np.all(g["ovf"] == 0)
+        x, v = oracle_predicted(w)
+        F, J = oracle.full(x, v, w.m, w.act)
+        ftol, jtol = TOL[mode]
+        assert rel_err(g["F"], F).max() <= ftol and rel_err(g["J"], J).max() <= jtol
+
+
+@pytest.mark.parametrize("cap", [0, 1, 7, 300])
+def test_everyone_a_neighbour_and_overflow(cap):
+    n = 700
+    w = inputs.cluster(n, 8, 8, cap)
+    w.h[:] = 1e4
+    g = gpu_run(w, "mixed", cap=cap)
+    assert g["status"] == 0
+    assert np.all(g["nnb"] == n - 1)
+    assert np.all(g["ovf"] == (1 if n - 1 > cap else 0))
+    assert np.all(g["F"] == 0) and np.all(g["J"] == 0)
+    if cap > 0:
+        o = oracle_run(w, cap=cap)
+        k = min(cap, n - 1)
+        assert np.array_equal(g["list"][:, :k], o["list"][:, :k])
+
+
+def test_empty_active_set_launches_nothing():
+    w = inputs.cluster(500, 9, 8, 16, act=np.zeros(0, dtype=np.int32))
+    g = gpu_run(w, "mixed")
+    assert g["status"] == 0 and g["launches"] == 0 and g["F"].shape == (0, 3)
+
+
+@pytest.mark.parametrize("mode", ["fp64", "mixed", "fp32"])
+def test_velocity_criterion(mode):
+    w = inputs.cluster(6000, 11, 48, 128, dtr_steps=(2.0**-5, 2.0**-6, 2.0**-7, 2.0**-8))
+    g = gpu_run(w, mode)
+    o = oracle_run(w)
+    compare(g, o, w.cap, mode, lists=(mode != "fp32"))
+
+
+@pytest.mark.parametrize("mode", ["fp64", "mixed"])
+def test_potential(mode):
+    w = inputs.cluster(5000, 12, 40, 96)
+    g = gpu_run(w, mode, pot=True)
+    compare(g, oracle_run(w, pot=True), w.cap, mode, pot=True)
+
+
+def test_j_range_offset_in_a_larger_context():
+    w = inputs.cluster(2500, 13, 30, 64)
+    with Context(w.n + 5000) as ctx:
+        g = gpu_run(w, "mixed", ctx=ctx, j_offset=777)
+    compare(g, oracle_run(w), w.cap, "mixed")
+
+
+def test_split_and_unsplit_paths_agree():
+    w = inputs.cluster(20000, 14, 64, 256, act=np.arange(0, 20000, 97, dtype=np.int32))
+    o = oracle_run(w)
+    one = gpu_run(w, "mixed", cfg=B.nb_kcfg(8, 4, 512, 1000))     # one split per i-block
+    many = gpu_run(w, "mixed", cfg=B.nb_kcfg(8, 4, 512, 1))       # one tile per split
+    assert one["launches"] == 1 and many["launches"] == 2
+    for g in (one, many):
+        compare(g, o, w.cap, "mixed")
+    assert np.array_equal(one["list"], many["list"])
+
+
+def _all_cfgs():
+    try:
+        build.build()
+        out = []
+        for mode in ("fp64", "mixed", "fp32"):
+            for i in range(B.nb_num_kernel_configs(mode_id(mode))):
+                out.append((mode, B.nb_get_kernel_config(mode_id(mode), i).as_tuple()))
+        return out
+    except Exception:   # no compiler: the list is empty and the module's fixture fails instead
+        return []
+
+
+@pytest.mark.parametrize("mode,cfg", _all_cfgs())
+def test_every_compiled_configuration(mode, cfg):
+    w = inputs.cluster(3100, 15, 40, 128, act=np.arange(0, 3100, 6, dtype=np.int32))
+    for split in (0, 1):
+        g = gpu_run(w, mode, cfg=B.nb_kcfg(cfg[0], cfg[1], cfg[2], split))
+        assert g["status"] == 0
+        compare(g, oracle_run(w), w.cap, mode, lists=(mode != "fp32"))
+
+
+def test_repeat_calls_are_bit_identical():
+    w = inputs.cluster(9000, 16, 50, 128)
+    a = gpu_run(w, "mixed")
+    b = gpu_run(w, "mixed")
+    for k in ("F", "J", "nnb", "list", "ovf"):
+        assert np.array_equal(a[k], b[k])
+
+
+# -------------------------------------------------------- batched / graph
+
+def _batch(nc=7, seed=40):
+    rng = np.random.default_rng(seed)
+    ws = []
+    for c in range(nc):
+        n = int(rng.integers(700, 3500))
+        na = int(rng.integers(1, n))
+        act = np.sort(rng.choice(n, na, replace=False)).astype(np.int32)
+        ws.append(inputs.cluster(n, seed * 100 + c, 40, 128, act=act))
+    return ws
+
+
+@pytest.mark.parametrize("mode", ["fp64", "mixed"])
+def test_batched_plan_and_graph(mode):
+    import torch
+    ws = _batch()
+    offs = np.cumsum([0] + [w.n + 13 for w in ws])   # gaps between the clusters' slots
+    with Context(int(offs[-1])) as ctx:
+        keep, cl = [], []
+        for w, off in zip(ws, offs):
+            d = upload(w)
+            ctx.predict(d["x0"], d["v0"], d["a0"], d["adot0"], d["m"], d["t0"], w.t, offset=int(off))
+            out = ctx.alloc_outputs(w.n_act, w.cap)
+            keep.append((d, out))
+            cl.append(B.nb_cluster(int(off), w.n, w.n_act, w.cap, d["act"].data_ptr(), d["h"].data_ptr(),
+                                   None, out["F"].data_ptr(), out["J"].data_ptr(), None,
+                                   out["nnb"].data_ptr(), out["list"].data_ptr(), out["ovf"].data_ptr()))
+        plan = B.nb_plan_create(ctx.h, cl, mode_id(mode))
+        try:
+            B.nb_plan_run(plan, ctx=ctx.h)
+            assert ctx.sync_status() == 0
+            first = [{k: v.cpu().numpy() for k, v in out.items() if v is not None} for _, out in keep]
+            for (w, g) in zip(ws, first):
+                compare(g, oracle_run(w), w.cap, mode)
+            for _, out in keep:
+                out["F"].zero_(); out["list"].fill_(-1); out["nnb"].fill_(-5)
+            stream = torch.cuda.Stream()
+            B.nb_plan_capture(plan, stream=stream, ctx=ctx.h)
+            B.nb_plan_launch(plan, stream=stream, ctx=ctx.h)
+            stream.synchronize()
+            assert ctx.sync_status() == 0
+            for (d, out), g in zip(keep, first):
+                for k in ("F", "J", "nnb", "list", "ovf"):
+                    assert np.array_equal(out[k].cpu().numpy(), g[k])
+        finally:
+            B.nb_plan_destroy(plan)
+
+
+# ------------------------------------------------------------- host step
+
+def test_host_step_matches_oracle():
+    import torch
+    w = inputs.cluster(8000, 17, 48, 128, act=np.arange(0, 8000, 3, dtype=np.int32))
+    pin = lambda a, dt=torch.float64: torch.as_tensor(np.ascontiguousarray(a), dtype=dt).pin_memory()
+    hx = {k: pin(getattr(w, k)) for k in ("x0", "v0", "a0", "adot0", "m", "t0", "h")}
+    act = pin(w.act, torch.int32)
+    F = torch.empty((w.n_act, 3), dtype=torch.float64).pin_memory()
+    J = torch.empty_like(F)
+    nnb = torch.empty(w.n_act, dtype=torch.int32).pin_memory()
+    lst = torch.full((w.n_act, w.cap), -1, dtype=torch.int32).pin_memory()
+    ovf = torch.empty(w.n_act, dtype=torch.uint8).pin_memory()
+    with Context(w.n) as ctx:
+        B.nb_step_host(ctx.h, w.n, hx["x0"], hx["v0"], hx["a0"], hx["adot0"], hx["m"], hx["t0"], w.t, w.n_act,
+                       act, hx["h"], None, w.cap, B.NB_MIXED, F, J, None, nnb, lst, ovf)
+    g = {"F": F.numpy(), "J": J.numpy(), "nnb": nnb.numpy(), "list": lst.numpy(), "ovf": ovf.numpy()}
+    compare(g, oracle_run(w), w.cap, "mixed")
+
+
+# ------------------------------------------------- device-side error paths
+
+def test_invalid_device_inputs_are_reported_not_faulted():
+    import torch
+    w = inputs.cluster(2000, 18, 20, 64, act=np.arange(0, 2000, 10, dtype=np.int32))
+    with Context(w.n) as ctx:
+        d = upload(w)
+        ctx.predict(d["x0"], d["v0"], d["a0"], d["adot0"], d["m"], d["t0"], w.t)
+        bad = d["act"].clone()
+        bad[3] = w.n + 5          # out of range
+        bad[7] = -1
+        h = d["h"].clone()
+        h[11] = -1.0              # negative radius
+        h[12] = float("nan")
+        out = ctx.regular_force(bad, h, w.n, cap=w.cap, mode="mixed")
+        assert ctx.sync_status() == B.NB_ERR_DEVICE_INPUT
+        # the context stays usable and the valid particles are still right
+        good = ctx.regular_force(d["act"], d["h"], w.n, cap=w.cap, mode="mixed")
+        assert ctx.sync_status() == 0
+        g = {k: v.cpu().numpy() for k, v in good.items() if v is not None}
+        compare(g, oracle_run(w), w.cap, "mixed")
+        o = {k: v.cpu().numpy() for k, v in out.items() if v is not None}
+        ok = np.setdiff1d(np.arange(w.n_act), [3, 7, 11, 12])
+        assert np.array_equal(o["nnb"][ok], g["nnb"][ok])
+
+
+def test_bounded_wait_times_out_cleanly():
+    """A copy barrier that can never complete (the test hook asks for more
+    bytes than are copied): every wait gives up after its bound, the kernel
+    returns and the status says NB_ERR_TIMEOUT; afterwards the context works."""
+    w = inputs.cluster(3000, 19, 20, 64, act=np.arange(0, 3000, 50, dtype=np.int32))
+    with Context(w.n) as ctx:
+        d = upload(w)
+        ctx.predict(d["x0"], d["v0"], d["a0"], d["adot0"], d["m"], d["t0"], w.t)
+        B.nb_debug_set_wait(ctx.h, 20_000_000, 16)        # 20 ms bound, 16 bytes never arrive
+        ctx.regular_force(d["act"], d["h"], w.n, cap=w.cap, mode="mixed")
+        assert ctx.sync_status() == B.NB_ERR_TIMEOUT
+        B.nb_debug_set_wait(ctx.h, 0, 0)
+        out = ctx.regular_force(d["act"], d["h"], w.n, cap=w.cap, mode="mixed")
+        assert ctx.sync_status() == 0
+        g = {k: v.cpu().numpy() for k, v in out.items() if v is not None}
+        compare(g, oracle_run(w), w.cap, "mixed")
+
+
+def test_argument_errors_are_host_side():
+    w = inputs.cluster(500, 20, 8, 16)
+    with Context(w.n) as ctx:
+        d = upload(w)
+        with pytest.raises(B.NbError) as e:      # nothing predicted yet
+            ctx.regular_force(d["act"], d["h"], w.n, cap=16, mode="mixed")
+        assert e.value.status == B.NB_ERR_STATE
+        ctx.predict(d["x0"], d["v0"], d["a0"], d["adot0"], d["m"], d["t0"], w.t, forms=B.NB_FORM_MIXED)
+        with pytest.raises(B.NbError) as e:      # FP64 form not written
+            ctx.regular_force(d["act"], d["h"], w.n, cap=16, mode="fp64")
+        assert e.value.status == B.NB_ERR_STATE
+        with pytest.raises(B.NbError) as e:      # j-range past the context
+            ctx.regular_force(d["act"], d["h"], w.n + 1, cap=16, mode="mixed")
+        assert e.value.status == B.NB_ERR_ARG
+
+
+# ------------------------------------------------------------ full sizes
+
+@pytest.fixture(scope="module")
+def cfg3():
+    return inputs.cached(inputs.config3)
+
+
+@pytest.mark.parametrize("mode", ["fp64", "mixed"])
+def test_config3_kroupa_131072_active_2048(cfg3, mode):
+    w = inputs.subset(cfg3, 2048, 3)
+    g = gpu_run(w, mode)
+    assert g["status"] == 0
+    compare(g, oracle_run(w), w.cap, mode)
+
+
+def test_config3_all_active_sampled(cfg3):
+    """The benchmark's workload (N = n_act = 131072, mixed form, default
+    configuration): 1024 sampled particles against the oracle one by one, and
+    every particle's count equal to the count its radius was built for."""
+    w = cfg3
+    g = gpu_run(w, "mixed")
+    assert g["status"] == 0
+    assert np.array_equal(g["nnb"], w.meta["K"])
+    rows = np.sort(np.random.default_rng(33).choice(w.n_act, 1024, replace=False))
+    eF, eJ = compare(g, oracle_run(w, rows=rows), w.cap, "mixed", rows=rows)
+
+
+@pytest.fixture(scope="module")
+def cfg5():
+    return inputs.cached(inputs.config5)
+
+
+def test_config5_offset_hard_pairs(cfg5):
+    """|x_c| = 1e3 and 10% hard pairs: the two-float and FP64 forms keep exact
+    lists; the plain FP32 form is only reported (it is expected to lose them)."""
+    w = inputs.subset(cfg5, 4096, 5)
+    o = oracle_run(w)
+    for mode in ("fp64", "mixed"):
+        g = gpu_run(w, mode)
+        assert g["status"] == 0
+        compare(g, o, w.cap, mode)
+    g = gpu_run(w, "fp32")
+    print("fp32 list mismatches at offset 1e3:", list_mismatches(g, o, w.cap),
+          "max force err", rel_err(g["F"], o["F"]).max())
