@@ -51,6 +51,12 @@ def parse_args():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-forms", action="store_true", help="skip the FP64/FP32 side measurements")
     ap.add_argument("--cpu-sample", type=int, default=4096, help="active particles in the oracle sample")
+    ap.add_argument("--no-e2e", action="store_true", help="skip the host-buffer measurement")
+    ap.add_argument("--config", default="", help="kernel tiling warps,ipw,jtile,packed[,split] "
+                                                 "(default: the library's default for the mode)")
+    ap.add_argument("--n", type=int, default=131072,
+                    help="j-particles (131072 = the benchmark workload; smaller N builds the same kind of "
+                         "cluster, used for profiling captures)")
     return ap.parse_args()
 
 
@@ -61,9 +67,13 @@ def dist_env():
     return rank, world, local
 
 
-def workload(n_act):
+def workload(n_act, n=131072):
     from paper_1205_1222_gb300 import inputs
-    w = inputs.cached(inputs.config3)
+    if n == 131072:
+        w = inputs.cached(inputs.config3)
+    else:
+        w = inputs.cached(inputs.cluster, n, 3, 100, 256, "hierarchy", 2.0**-10, "kroupa",
+                          key=f"kroupa_plummer_n{n}")
     if n_act and n_act < w.n:
         w = inputs.subset(w, n_act, 3)
     return w
@@ -205,7 +215,7 @@ def job_value(interactions_per_rank, world, ms_max):
 class Runner:
     """Device-resident inputs and outputs of one workload, and one step."""
 
-    def __init__(self, w, mode, device):
+    def __init__(self, w, mode, device, cfg=""):
         import numpy as np
         import torch
 
@@ -220,6 +230,11 @@ class Runner:
         self.stream = torch.cuda.current_stream(device)
         self.form = B.MODE_FORM[self.mode]
         self.launches = 0
+        if cfg:
+            f = [int(x) for x in cfg.split(",")]
+            B.nb_set_kernel_config(self.ctx.h, self.mode, B.nb_kcfg(f[0], f[1], f[2], f[4] if len(f) > 4 else 0,
+                                                                    f[3]))
+        self.cfg = B.nb_get_active_config(self.ctx.h, self.mode).as_tuple()
 
     def predict(self):
         d = self.d
@@ -338,8 +353,8 @@ def run_ours(args):
         build.build()
     if world > 1:
         torch.distributed.barrier()
-    w = workload(args.n_act)
-    r = Runner(w, args.mode, device)
+    w = workload(args.n_act, args.n)
+    r = Runner(w, args.mode, device, args.config)
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=f"cuda:{device}")
     for _ in range(max(args.warmup, 3)):
         r.predict()
@@ -395,7 +410,8 @@ def run_ours(args):
     line["roofline"] = {
         "bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
         "traffic": profiled_traffic(),
-        "kernel": "regf_kernel (regular force + jerk + list), one launch per step",
+        "kernel": "regular force + jerk + list kernel, one launch per step; tiling (warps, ipw, jtile, "
+                  f"split, packed) = {r.cfg}",
         "kernel_ms": fms,
         "peak_basis": f"{sm} SMs x 128 FP32 lanes x 2 flops x {mhz:.0f} MHz ({mhz_src}); "
                       f"{FLOPS_PER_INTERACTION} flops per interaction",
@@ -427,7 +443,8 @@ def run_ours(args):
             outs[mode] = rr.outputs()
             rr.close()
         line["forms"] = forms
-    line["e2e"] = e2e_measure(w, args.mode, device, max(1, min(args.steps, 5)))
+    if not args.no_e2e:
+        line["e2e"] = e2e_measure(w, args.mode, device, max(1, min(args.steps, 5)))
     if not args.no_cpu_baseline:
         base, o, rows = cpu_baseline(w, args.cpu_sample)
         line["cpu_baseline"] = base
@@ -445,7 +462,7 @@ def run_reference(args):
     import numpy as np
 
     import oracle
-    w = workload(args.n_act)
+    w = workload(args.n_act, args.n)
     x, v = oracle.predict(w.x0, w.v0, w.a0, w.adot0, w.t0, w.t)
     threads = oracle.default_threads()
     sample = min(256, w.n_act)

@@ -76,6 +76,8 @@ typedef struct nb_kcfg {
     int32_t ipw;        /* active particles per warp (the i-tile of a warp)             */
     int32_t jtile;      /* j-particles per shared-memory tile                            */
     int32_t split;      /* j-tiles per work item; 0 = choose from the grid size          */
+    int32_t packed;     /* 1: pair arithmetic of two i-particles per f32x2 instruction
+                         * (float forms); 0: one FP32 or FP64 operation per pair term   */
 } nb_kcfg;
 
 /* One independent cluster of a batched call (host struct; the pointers in it
@@ -182,7 +184,7 @@ int nb_plan_launches(const nb_plan *plan);
  * active set from host memory, predict (only the form `mode` needs), compute
  * the regular force, copy the results back into host memory and wait for
  * them.  All array arguments are HOST pointers (pinned memory gives
- * asynchronous copies).  Same meaning and errors as nb_predict followed by
+ * asynchronous copies).  List slots past min(nnb, cap) are returned as -1.  Same meaning and errors as nb_predict followed by
  * nb_regular_force on j-range [0, n); also returns the device status. */
 int nb_step_host(nb_ctx *ctx, int64_t n, const double *x0, const double *v0, const double *a0,
                  const double *adot0, const double *m, const double *t0, double t,

@@ -48,10 +48,13 @@ class NbError(RuntimeError):
 
 class nb_kcfg(ctypes.Structure):
     _fields_ = [("warps", ctypes.c_int32), ("ipw", ctypes.c_int32), ("jtile", ctypes.c_int32),
-                ("split", ctypes.c_int32)]
+                ("split", ctypes.c_int32), ("packed", ctypes.c_int32)]
 
     def as_tuple(self):
-        return (self.warps, self.ipw, self.jtile, self.split)
+        return (self.warps, self.ipw, self.jtile, self.split, self.packed)
+
+    def __repr__(self):
+        return "nb_kcfg(warps=%d, ipw=%d, jtile=%d, split=%d, packed=%d)" % self.as_tuple()
 
 
 class nb_cluster(ctypes.Structure):

@@ -73,6 +73,8 @@ struct nb_ctx {
     double4_32a *pos64 = nullptr, *vel64 = nullptr;
     float4 *mx_hi = nullptr, *mx_lo = nullptr, *mv_hi = nullptr, *mv_lo = nullptr;
     float4 *pos32 = nullptr, *vel32 = nullptr;
+    float4 *pim[7] = {};   // pair-interleaved two-float streams, (n_max + 1) / 2 j-pairs each
+    float4 *pif[4] = {};   // pair-interleaved FP32 streams
     int forms_valid = 0;
     int *d_status = nullptr;
     void *scratch = nullptr;
@@ -126,8 +128,8 @@ nb_kcfg default_cfg(int mode)
 {
     Registry &r = registry();
     for (const auto &e : r.all)
-        if (e.mode == mode && e.flags == 0) return nb_kcfg{e.warps, e.ipw, e.jtile, 0};
-    return nb_kcfg{0, 0, 0, 0};
+        if (e.mode == mode && e.flags == 0) return nb_kcfg{e.warps, e.ipw, e.jtile, 0, e.packed};
+    return nb_kcfg{0, 0, 0, 0, 0};
 }
 
 // Index of the kernel for (mode, cfg, flags); falls back to the mode's default
@@ -138,7 +140,7 @@ int find_entry(int mode, const nb_kcfg &cfg, int flags)
     for (size_t i = 0; i < r.all.size(); i++) {
         const auto &e = r.all[i];
         if (e.mode == mode && e.flags == flags && e.warps == cfg.warps && e.ipw == cfg.ipw &&
-            e.jtile == cfg.jtile)
+            e.jtile == cfg.jtile && e.packed == cfg.packed)
             return static_cast<int>(i);
     }
     for (size_t i = 0; i < r.all.size(); i++)
@@ -205,6 +207,7 @@ void carve_scratch(ClusterDesc &d, char *base)
     d.plist = reinterpret_cast<int32_t *>(base);
 }
 
+// Per-particle (SoA) streams of a form.
 nb::JSet jset(const nb_ctx *c, int mode)
 {
     nb::JSet js{};
@@ -212,6 +215,26 @@ nb::JSet jset(const nb_ctx *c, int mode)
     else if (mode == NB_MIXED) { js.s[0] = c->mx_hi; js.s[1] = c->mx_lo; js.s[2] = c->mv_hi; js.s[3] = c->mv_lo; }
     else { js.s[0] = c->pos32; js.s[1] = c->vel32; }
     return js;
+}
+
+// Streams the j-tiles of kernel entry e are copied from.
+nb::JSet tile_streams(const nb_ctx *c, int mode, const KernelEntry &e)
+{
+    if (e.packed != 2) return jset(c, mode);
+    nb::JSet js{};
+    if (mode == NB_MIXED) for (int k = 0; k < 7; k++) js.s[k] = c->pim[k];
+    else for (int k = 0; k < 4; k++) js.s[k] = c->pif[k];
+    return js;
+}
+
+// The j-pair kernels read pairs (2P, 2P+1); a j-range starting at an odd
+// slot is served by the first compiled kernel of another layout.
+int layout_fallback(int mode, int idx, int flags)
+{
+    Registry &r = registry();
+    for (size_t i = 0; i < r.all.size(); i++)
+        if (r.all[i].mode == mode && r.all[i].flags == flags && r.all[i].packed != 2) return static_cast<int>(i);
+    return idx;
 }
 
 int grow_scratch(nb_ctx *ctx, size_t need, cudaStream_t st)
@@ -296,8 +319,9 @@ int run_single(nb_ctx *ctx, const Call &c, const nb_kcfg *cfg_override, cudaStre
     DeviceGuard guard(ctx->device);
     const nb_kcfg cfg = cfg_override ? *cfg_override : (ctx->cfg_set[c.mode] ? ctx->cfg[c.mode] : default_cfg(c.mode));
     const int flags = (c.dtr ? 1 : 0) | (c.pot ? 2 : 0);
-    const int idx = find_entry(c.mode, cfg, flags);
+    int idx = find_entry(c.mode, cfg, flags);
     if (idx < 0) { ctx->err = "no kernel for this mode"; return NB_ERR_UNSUPPORTED; }
+    if (registry().all[idx].packed == 2 && (c.j_begin & 1)) idx = layout_fallback(c.mode, idx, flags);
     int occ = 0;
     rc = entry_occupancy(ctx, idx, &occ);
     if (rc != NB_OK) return rc;
@@ -310,7 +334,8 @@ int run_single(nb_ctx *ctx, const Call &c, const nb_kcfg *cfg_override, cudaStre
     carve_scratch(d, static_cast<char *>(ctx->scratch));
 
     nb::RegfParams p{};
-    p.js = jset(ctx, c.mode);
+    p.js = tile_streams(ctx, c.mode, e);
+    p.soa = jset(ctx, c.mode);
     p.d0 = d;
     p.table = nullptr;
     p.item_begin = nullptr;
@@ -386,6 +411,9 @@ int nb_create(nb_ctx **out, int device, int64_t n_max)
     alloc(reinterpret_cast<void **>(&c->mv_lo), n * sizeof(float4));
     alloc(reinterpret_cast<void **>(&c->pos32), n * sizeof(float4));
     alloc(reinterpret_cast<void **>(&c->vel32), n * sizeof(float4));
+    const size_t npairs = (n + 1) / 2;
+    for (int k = 0; k < 7; k++) alloc(reinterpret_cast<void **>(&c->pim[k]), npairs * sizeof(float4));
+    for (int k = 0; k < 4; k++) alloc(reinterpret_cast<void **>(&c->pif[k]), npairs * sizeof(float4));
     alloc(reinterpret_cast<void **>(&c->d_status), sizeof(int));
     if (rc == NB_OK && cudaMemset(c->d_status, 0, sizeof(int)) != cudaSuccess) rc = NB_ERR_CUDA;
     if (rc == NB_OK && cudaDeviceGetAttribute(&c->sm_count, cudaDevAttrMultiProcessorCount, device) != cudaSuccess)
@@ -406,6 +434,10 @@ void nb_destroy(nb_ctx *c)
     void *bufs[] = {c->pos64, c->vel64, c->mx_hi, c->mx_lo, c->mv_hi, c->mv_lo, c->pos32, c->vel32,
                     c->d_status, c->scratch, c->stage};
     for (void *b : bufs)
+        if (b) cudaFree(b);
+    for (float4 *b : c->pim)
+        if (b) cudaFree(b);
+    for (float4 *b : c->pif)
         if (b) cudaFree(b);
     delete c;
 }
@@ -430,6 +462,8 @@ static int predict_impl(nb_ctx *ctx, int64_t offset, int64_t n, const double *x0
     p.pos64 = ctx->pos64; p.vel64 = ctx->vel64;
     p.mx_hi = ctx->mx_hi; p.mx_lo = ctx->mx_lo; p.mv_hi = ctx->mv_hi; p.mv_lo = ctx->mv_lo;
     p.pos32 = ctx->pos32; p.vel32 = ctx->vel32;
+    for (int k = 0; k < 7; k++) p.pim[k] = ctx->pim[k];
+    for (int k = 0; k < 4; k++) p.pif[k] = ctx->pif[k];
     nb::launch_predict(p, st);
     NB_CUDA(ctx, cudaGetLastError());
     ctx->forms_valid = forms;   // forms not rewritten are stale now
@@ -539,7 +573,7 @@ int nb_get_kernel_config(int mode, int index, nb_kcfg *out)
     int n = 0;
     for (const auto &e : registry().all)
         if (e.mode == mode && e.flags == 0) {
-            if (n == index) { *out = nb_kcfg{e.warps, e.ipw, e.jtile, 0}; return NB_OK; }
+            if (n == index) { *out = nb_kcfg{e.warps, e.ipw, e.jtile, 0, e.packed}; return NB_OK; }
             n++;
         }
     return NB_ERR_ARG;
@@ -552,7 +586,7 @@ int nb_set_kernel_config(nb_ctx *ctx, int mode, const nb_kcfg *cfg)
     if (cfg->split < 0) return NB_ERR_ARG;
     for (const auto &e : registry().all)
         if (e.mode == mode && e.flags == 0 && e.warps == cfg->warps && e.ipw == cfg->ipw &&
-            e.jtile == cfg->jtile) {
+            e.jtile == cfg->jtile && e.packed == cfg->packed) {
             ctx->cfg[mode] = *cfg;
             ctx->cfg_set[mode] = true;
             return NB_OK;
@@ -658,6 +692,8 @@ int nb_step_host(nb_ctx *ctx, int64_t n, const double *x0, const double *v0, con
                         d_in + 13 * nn, t, mode_forms(mode), st);
     if (rc != NB_OK) return rc;
     int launches = 1;
+    if (n_act > 0 && cap > 0)   // list slots past min(nnb, cap) come back as -1
+        NB_CUDA(ctx, cudaMemsetAsync(s + o_list, 0xff, na * static_cast<size_t>(cap) * sizeof(int32_t), st));
     if (n_act > 0) {
         rc = nb_regular_force(ctx, 0, n, n_act, reinterpret_cast<int32_t *>(s + o_act),
                               reinterpret_cast<double *>(s + o_h),
@@ -712,8 +748,11 @@ int nb_plan_create(nb_ctx *ctx, int32_t n_clusters, const nb_cluster *cl, int mo
         flags |= (cl[c].dtr ? 1 : 0) | (cl[c].pot ? 2 : 0);
     }
     const nb_kcfg cfg = cfg_in ? *cfg_in : (ctx->cfg_set[mode] ? ctx->cfg[mode] : default_cfg(mode));
-    const int idx = find_entry(mode, cfg, flags);
+    int idx = find_entry(mode, cfg, flags);
     if (idx < 0) return NB_ERR_UNSUPPORTED;
+    bool odd = false;
+    for (int c = 0; c < n_clusters; c++) odd |= (cl[c].j_begin & 1) != 0;
+    if (registry().all[idx].packed == 2 && odd) idx = layout_fallback(mode, idx, flags);
     int occ = 0;
     int rc = entry_occupancy(ctx, idx, &occ);
     if (rc != NB_OK) return rc;
@@ -810,7 +849,8 @@ int nb_plan_run(nb_plan *p, nb_stream_t stream)
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     if (p->n_items > 0) {
         nb::RegfParams rp{};
-        rp.js = jset(ctx, p->mode);
+        rp.js = tile_streams(ctx, p->mode, *p->e);
+        rp.soa = jset(ctx, p->mode);
         rp.table = p->d_table;
         rp.item_begin = p->d_item_begin;
         rp.n_clusters = static_cast<int32_t>(p->descs.size());

@@ -5,7 +5,9 @@
 //    paper does this on the host before GPUNB_SEND) and writes the stored
 //    copies the force kernels read: FP64 double4 (x,y,z,m) + (vx,vy,vz,0),
 //    two-float float4 hi/lo pairs of position and velocity (mass in the
-//    hi-position w), and plain FP32 float4 copies.
+//    hi-position w), and plain FP32 float4 copies; the two float forms are
+//    also written pair-interleaved (float4 k of j-pair P holds components of
+//    slots 2P and 2P+1) for the j-pair packed kernels.
 //  * merge_kernel: one warp per active particle of a cluster whose j-range
 //    was split over several work items; sums the per-split FP64 partial
 //    force, jerk and potential in a fixed order and concatenates the
@@ -52,6 +54,36 @@ __global__ void predict_kernel(const PredParams p)
         p.mx_lo[s] = make_float4(xl[0], xl[1], xl[2], 0.f);
         p.mv_hi[s] = make_float4(vh[0], vh[1], vh[2], 0.f);
         p.mv_lo[s] = make_float4(vl[0], vl[1], vl[2], 0.f);
+    }
+    if (p.forms & 2) {   // pair-interleaved copy: half h of j-pair s / 2
+        const int64_t P = s >> 1;
+        const int h = static_cast<int>(s & 1);
+        float xh[3], xl[3], vh[3], vl[3];
+        for (int k = 0; k < 3; k++) {
+            xh[k] = __double2float_rn(x[k]);
+            xl[k] = __double2float_rn(x[k] - static_cast<double>(xh[k]));
+            vh[k] = __double2float_rn(v[k]);
+            vl[k] = __double2float_rn(v[k] - static_cast<double>(vh[k]));
+        }
+        const float vals[14] = {xh[0], xh[1], xh[2], __double2float_rn(m), xl[0], xl[1], xl[2],
+                                vh[0], vh[1], vh[2], vl[0], vl[1], vl[2], 0.f};
+        for (int q = 0; q < 7; q++) {
+            float *f = reinterpret_cast<float *>(p.pim[q] + P);
+            f[h] = vals[2 * q];
+            f[2 + h] = vals[2 * q + 1];
+        }
+    }
+    if (p.forms & 4) {
+        const int64_t P = s >> 1;
+        const int h = static_cast<int>(s & 1);
+        const float vals[8] = {__double2float_rn(x[0]), __double2float_rn(x[1]), __double2float_rn(x[2]),
+                               __double2float_rn(m), __double2float_rn(v[0]), __double2float_rn(v[1]),
+                               __double2float_rn(v[2]), 0.f};
+        for (int q = 0; q < 4; q++) {
+            float *f = reinterpret_cast<float *>(p.pif[q] + P);
+            f[h] = vals[2 * q];
+            f[2 + h] = vals[2 * q + 1];
+        }
     }
     if (p.forms & 4) {
         p.pos32[s] = make_float4(__double2float_rn(x[0]), __double2float_rn(x[1]),

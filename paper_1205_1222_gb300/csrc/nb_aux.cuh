@@ -17,6 +17,8 @@ struct PredParams {
     double4_32a *pos64, *vel64;
     float4 *mx_hi, *mx_lo, *mv_hi, *mv_lo;
     float4 *pos32, *vel32;
+    float4 *pim[7];    // pair-interleaved two-float streams (j-pair P = slot / 2)
+    float4 *pif[4];    // pair-interleaved FP32 streams
 };
 
 struct MergeParams {
@@ -36,6 +38,8 @@ struct KernelEntry {
     int mode;        // 0 FP64, 1 MIXED, 2 FP32
     int warps, ipw, jtile;
     int flags;       // bit 0: velocity criterion, bit 1: potential
+    int packed;      // 0: scalar kernel (nb_regf.cuh), 1: f32x2 over i-pairs (nb_regf2.cuh),
+                     // 2: f32x2 over j-pairs on the pair-interleaved streams (nb_regf3.cuh)
     const void *fn;
     int smem;        // dynamic shared memory bytes
 };

@@ -16,7 +16,7 @@ enum : int {
 
 // Predicted j-set of one precision form: base pointers of its streams.
 struct JSet {
-    const void *s[4];
+    const void *s[8];
 };
 
 // One cluster of a regular-force launch, as the kernels see it.
@@ -46,7 +46,8 @@ struct ClusterDesc {
 };
 
 struct RegfParams {
-    JSet js;
+    JSet js;                      // streams the j-tiles are copied from
+    JSet soa;                     // per-particle (SoA) streams of the same form, for the i-values
     ClusterDesc d0;               // used when table == nullptr
     const ClusterDesc *table;     // device table of clusters (batched launch)
     const int64_t *item_begin;    // [n_clusters] copy of table[c].item_begin for the search

@@ -1,0 +1,396 @@
+// j-pair packed variant of the regular-force kernel (Sec. 3.3 step (vi),
+// criterion of Sec. 3.2) for the float forms.
+//
+// The f32x2 instructions of Blackwell (add/sub/mul/fma on two FP32 values in
+// a 64-bit register pair) are fed with pairs of j-particles: every lane takes
+// the two consecutive j of one j-pair per step, so a warp covers 64 j per
+// step, and the i-particle values are broadcast to both halves once per work
+// item.  The predicted j-set is stored pair-interleaved for this kernel: for
+// j-pair P (slots 2P, 2P+1) stream k holds one float4 with two components of
+// both particles, e.g. (x_a, x_b, y_a, y_b), so one 128-bit shared-memory
+// load yields two ready register pairs and no lane ever moves a value into a
+// pair.  Everything else follows nb_regf2.cuh: the NST-stage TMA ring
+// released by the last warp out, float-float totals in shared memory,
+// ballot + popc list compaction (here over the interleaved (lane, half)
+// order, which is ascending j).
+#pragma once
+
+#include <cfloat>
+
+#include "nb_regf2.cuh"
+
+namespace nb {
+
+// Two-float (mixed) form, pair-interleaved: 7 float4 streams per j-pair
+//   q0 (xh_a, xh_b, yh_a, yh_b)  q1 (zh_a, zh_b, m_a, m_b)  q2 (xl_a, xl_b, yl_a, yl_b)
+//   q3 (zl_a, zl_b, vxh_a, vxh_b)  q4 (vyh_a, vyh_b, vzh_a, vzh_b)
+//   q5 (vxl_a, vxl_b, vyl_a, vyl_b)  q6 (vzl_a, vzl_b, 0, 0)
+struct PairMixed {
+    static constexpr int NS = 7;
+    struct IB {   // one i-particle, negated, broadcast to both halves
+        f2 nxh[3], nxl[3], nvh[3], nvl[3], h2, dtr;
+    };
+    struct JP {   // one j-pair
+        f2 xh[3], m, xl[3], vh[3], vl[3];
+    };
+    template <int NP>
+    static __device__ __forceinline__ void load_j(JP &s, const unsigned char *st, int pl)
+    {
+        const ulonglong2 *q = reinterpret_cast<const ulonglong2 *>(st);
+        const ulonglong2 a = q[pl], b = q[NP + pl], c = q[2 * NP + pl], d = q[3 * NP + pl];
+        const ulonglong2 e = q[4 * NP + pl], f = q[5 * NP + pl], g = q[6 * NP + pl];
+        s.xh[0] = a.x; s.xh[1] = a.y; s.xh[2] = b.x; s.m = b.y;
+        s.xl[0] = c.x; s.xl[1] = c.y; s.xl[2] = d.x;
+        s.vh[0] = d.y; s.vh[1] = e.x; s.vh[2] = e.y;
+        s.vl[0] = f.x; s.vl[1] = f.y; s.vl[2] = g.x;
+    }
+    // Replace the invalid half(s) of a pair by a zero-mass particle far away.
+    static __device__ __forceinline__ void mask(JP &s, bool va, bool vb)
+    {
+        auto fix = [&](f2 &v, float far) {
+            float a, b;
+            up(v, a, b);
+            v = pk(va ? a : far, vb ? b : far);
+        };
+        for (int c = 0; c < 3; c++) {
+            fix(s.xh[c], FAR_F);
+            fix(s.xl[c], 0.f);
+            fix(s.vh[c], 0.f);
+            fix(s.vl[c], 0.f);
+        }
+        fix(s.m, 0.f);
+    }
+    static __device__ __forceinline__ void set_i(IB &ib, const JSet &soa, int64_t slot, float h2, float dtr)
+    {
+        FormMixed::IS a;
+        FormMixed::clear_i(a);
+        if (slot >= 0) FormMixed::load_i(a, soa, slot);
+        for (int c = 0; c < 3; c++) {
+            ib.nxh[c] = bc(-a.xh[c]);
+            ib.nxl[c] = bc(-a.xl[c]);
+            ib.nvh[c] = bc(-a.vh[c]);
+            ib.nvl[c] = bc(-a.vl[c]);
+        }
+        ib.h2 = bc(h2);
+        ib.dtr = bc(dtr);
+    }
+    template <bool VC, bool POT>
+    static __device__ __forceinline__ void pair(const IB &i, const JP &j, Acc2 &a, bool &fa, bool &fb)
+    {
+        const f2 dx = add2(add2(j.xh[0], i.nxh[0]), add2(j.xl[0], i.nxl[0]));
+        const f2 dy = add2(add2(j.xh[1], i.nxh[1]), add2(j.xl[1], i.nxl[1]));
+        const f2 dz = add2(add2(j.xh[2], i.nxh[2]), add2(j.xl[2], i.nxl[2]));
+        const f2 ux = add2(add2(j.vh[0], i.nvh[0]), add2(j.vl[0], i.nvl[0]));
+        const f2 uy = add2(add2(j.vh[1], i.nvh[1]), add2(j.vl[1], i.nvl[1]));
+        const f2 uz = add2(add2(j.vh[2], i.nvh[2]), add2(j.vl[2], i.nvl[2]));
+        tail2<VC, POT>(i.h2, i.dtr, j.m, dx, dy, dz, ux, uy, uz, a, fa, fb);
+    }
+};
+
+// Plain FP32 form, pair-interleaved: 4 float4 streams per j-pair
+//   q0 (x_a, x_b, y_a, y_b)  q1 (z_a, z_b, m_a, m_b)  q2 (vx_a, vx_b, vy_a, vy_b)  q3 (vz_a, vz_b, 0, 0)
+struct PairFP32 {
+    static constexpr int NS = 4;
+    struct IB {
+        f2 nx[3], nv[3], h2, dtr;
+    };
+    struct JP {
+        f2 x[3], m, v[3];
+    };
+    template <int NP>
+    static __device__ __forceinline__ void load_j(JP &s, const unsigned char *st, int pl)
+    {
+        const ulonglong2 *q = reinterpret_cast<const ulonglong2 *>(st);
+        const ulonglong2 a = q[pl], b = q[NP + pl], c = q[2 * NP + pl], d = q[3 * NP + pl];
+        s.x[0] = a.x; s.x[1] = a.y; s.x[2] = b.x; s.m = b.y;
+        s.v[0] = c.x; s.v[1] = c.y; s.v[2] = d.x;
+    }
+    static __device__ __forceinline__ void mask(JP &s, bool va, bool vb)
+    {
+        auto fix = [&](f2 &v, float far) {
+            float a, b;
+            up(v, a, b);
+            v = pk(va ? a : far, vb ? b : far);
+        };
+        for (int c = 0; c < 3; c++) {
+            fix(s.x[c], FAR_F);
+            fix(s.v[c], 0.f);
+        }
+        fix(s.m, 0.f);
+    }
+    static __device__ __forceinline__ void set_i(IB &ib, const JSet &soa, int64_t slot, float h2, float dtr)
+    {
+        FormFP32::IS a;
+        FormFP32::clear_i(a);
+        if (slot >= 0) FormFP32::load_i(a, soa, slot);
+        for (int c = 0; c < 3; c++) {
+            ib.nx[c] = bc(-a.x[c]);
+            ib.nv[c] = bc(-a.v[c]);
+        }
+        ib.h2 = bc(h2);
+        ib.dtr = bc(dtr);
+    }
+    template <bool VC, bool POT>
+    static __device__ __forceinline__ void pair(const IB &i, const JP &j, Acc2 &a, bool &fa, bool &fb)
+    {
+        tail2<VC, POT>(i.h2, i.dtr, j.m, add2(j.x[0], i.nx[0]), add2(j.x[1], i.nx[1]), add2(j.x[2], i.nx[2]),
+                       add2(j.v[0], i.nv[0]), add2(j.v[1], i.nv[1]), add2(j.v[2], i.nv[2]), a, fa, fb);
+    }
+};
+
+template <class Fm, int W, int I, int JT>
+struct PairLayout {
+    static constexpr int NST = 4;                                  // stages of the j-tile ring
+    static constexpr int NP = JT / 2;                              // j-pairs per tile
+    static constexpr int STAGE = Fm::NS * 16 * NP;
+    static constexpr int STAGES = 128;                             // barriers + release counters first
+    static constexpr int TOT = STAGES + NST * STAGE;
+    __host__ __device__ static constexpr int tot_bytes(bool pot) { return W * I * (pot ? 7 : 6) * 32 * 16; }
+    __host__ __device__ static constexpr int cnt(bool pot) { return TOT + tot_bytes(pot); }
+    __host__ __device__ static constexpr int gi(bool pot) { return cnt(pot) + W * I * 4; }
+    __host__ __device__ static constexpr int desc(bool pot) { return gi(pot) + W * I * 4; }
+    __host__ __device__ static constexpr int bytes(bool pot)
+    {
+        return desc(pot) + W * static_cast<int>(sizeof(ClusterDesc));
+    }
+};
+
+template <class Fm, int W, int I, int JT>
+constexpr int pair_smem_bytes(bool pot)
+{
+    return PairLayout<Fm, W, I, JT>::bytes(pot);
+}
+
+// Copy the pair-interleaved tile at cursor c into ring slot seq % NST.  The
+// j-range starts at an even slot (checked on the host), so tile t covers
+// j-pairs (jb + t*JT)/2 ... and a ragged tail copies ceil(count/2) pairs.
+template <class Fm, int JT, int NST>
+__device__ __forceinline__ void issue_pairs(const RegfParams &p, const TileCursor &c, uint32_t seq, uint64_t *full,
+                                            unsigned char *stages)
+{
+    constexpr int NP = JT / 2;
+    constexpr int STAGE = Fm::NS * 16 * NP;
+    const int s = seq % NST;
+    uint64_t *b = &full[s];
+    unsigned char *st = stages + s * STAGE;
+    const int count = min(JT, c.nj - c.tile * JT);
+    const uint32_t bytes = static_cast<uint32_t>((count + 1) / 2) * 16;
+    mbar_arrive_expect_tx(b, bytes * Fm::NS + p.extra_tx);
+    const int64_t first = (c.jb + static_cast<int64_t>(c.tile) * JT) / 2;
+#pragma unroll
+    for (int k = 0; k < Fm::NS; k++)
+        tma_bulk_g2s(st + k * NP * 16, static_cast<const unsigned char *>(p.js.s[k]) + first * 16, bytes, b);
+}
+
+template <class Fm, int W, int I, int JT, int FLAGS, int MINB>
+__global__ void __launch_bounds__(W * 32, MINB) regf3_kernel(const RegfParams p)
+{
+    using L = PairLayout<Fm, W, I, JT>;
+    constexpr bool VC = (FLAGS & 1) != 0;
+    constexpr bool POT = (FLAGS & 2) != 0;
+    constexpr int NC = POT ? 7 : 6;
+    constexpr int NST = L::NST;
+    constexpr int NP = L::NP;
+    constexpr int STEPS = NP / 32;                                // a step covers 64 j
+    constexpr int FOLD_STEPS = 64;                                // steps (128 j per lane) per FP32 partial
+    constexpr int FOLD_TILES = STEPS >= FOLD_STEPS ? 1 : FOLD_STEPS / STEPS;
+    using JP = typename Fm::JP;
+    using IB = typename Fm::IB;
+
+    extern __shared__ __align__(128) unsigned char smem[];
+    uint64_t *full = reinterpret_cast<uint64_t *>(smem);
+    int *rel = reinterpret_cast<int *>(smem + 8 * NST);
+    unsigned char *stages = smem + L::STAGES;
+    float4 *s_tot = reinterpret_cast<float4 *>(smem + L::TOT);
+    int *s_cnt = reinterpret_cast<int *>(smem + L::cnt(POT));
+    int *s_gi = reinterpret_cast<int *>(smem + L::gi(POT));
+    ClusterDesc *s_d = reinterpret_cast<ClusterDesc *>(smem + L::desc(POT));
+
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    TileCursor la;
+    la.item = blockIdx.x;
+    cursor_set(p, la);
+    if (tid == 0) {
+        for (int s = 0; s < NST; s++) {
+            mbar_init(&full[s], 1);
+            rel[s] = 0;
+        }
+        fence_mbar_init();
+        TileCursor c0 = la;
+        for (int q = 0; q < NST && c0.item < p.n_items; ++q) {
+            issue_pairs<Fm, JT, NST>(p, c0, q, full, stages);
+            cursor_next(p, c0);
+        }
+    }
+    for (int q = 0; q < NST && la.item < p.n_items; ++q) cursor_next(p, la);   // look-ahead = sequence NST
+    __syncthreads();
+
+    uint32_t g = 0;
+    bool aborted = false;
+    float4 *mytot = s_tot + warp * I * NC * 32 + lane;   // + (i * NC + comp) * 32: (hi_a, hi_b, lo_a, lo_b)
+    int *mycnt = s_cnt + warp * I;
+    int *mygi = s_gi + warp * I;
+    ClusterDesc &d = s_d[warp];
+
+    for (int64_t item = blockIdx.x; item < p.n_items && !aborted; item += gridDim.x) {
+        if (lane == 0) d = p.table ? p.table[find_cluster(p, item)] : p.d0;
+        __syncwarp();
+        const int64_t local = item - d.item_begin;
+        const int ib = static_cast<int>(local / d.n_split);
+        const int sp = static_cast<int>(local - static_cast<int64_t>(ib) * d.n_split);
+        const int tb = sp * d.tiles_per_split;
+        const int te = min(tb + d.tiles_per_split, d.n_tiles);
+
+        IB ipart[I];
+        Acc2 acc[I];
+        const int i0 = (ib * W + warp) * I;
+#pragma unroll
+        for (int k = 0; k < I; k++) {
+            const int idx = i0 + k;
+            int64_t slot = -1;
+            float h2v = -1.f, dtv = 0.f;
+            int gi = -1;
+            if (idx < d.n_act) {
+                const int a = d.act[idx];
+                const double hv = d.h[idx];
+                if (a >= 0 && a < d.n_j && hv >= 0.0 && hv <= DBL_MAX) {
+                    gi = a;
+                    slot = d.j_begin + a;
+                    h2v = fmaxf(__double2float_rn(hv * hv), FLT_MIN);   // self (r2 = 0) is inside
+                    dtv = (VC && d.dtr) ? __double2float_rn(d.dtr[idx]) : 0.f;
+                } else if (lane == 0) {
+                    atomicOr(p.status, DEV_BAD_INPUT);
+                }
+            }
+            if (lane == 0) { mygi[k] = gi; mycnt[k] = 0; }
+            Fm::set_i(ipart[k], p.soa, slot, h2v, dtv);
+            for (int c = 0; c < 3; c++) acc[k].f[c] = acc[k].j[c] = 0ull;
+            acc[k].p = 0ull;
+            for (int c = 0; c < NC; c++) mytot[(k * NC + c) * 32] = make_float4(0.f, 0.f, 0.f, 0.f);
+        }
+        __syncwarp();
+
+        for (int t = tb; t < te; ++t, ++g) {
+            const int s = g % NST;
+            if (!mbar_wait_bounded(&full[s], (g / NST) & 1, p.wait_ns)) { aborted = true; break; }
+            const unsigned char *st = stages + s * L::STAGE;
+            const int jt0 = t * JT;
+            const int count = min(JT, d.n_j - jt0);
+
+            auto step = [&](int k, bool tail) {
+                const int pl = k * 32 + lane;
+                JP jp;
+                Fm::template load_j<NP>(jp, st, pl);
+                if (tail) Fm::mask(jp, 2 * pl < count, 2 * pl + 1 < count);
+                bool fa[I], fb[I];
+                bool any = false;
+#pragma unroll
+                for (int q = 0; q < I; q++) {
+                    Fm::template pair<VC, POT>(ipart[q], jp, acc[q], fa[q], fb[q]);
+                    any |= fa[q] | fb[q];
+                }
+                if (__any_sync(0xffffffffu, any)) {
+                    const int ja = jt0 + 2 * pl;
+#pragma unroll
+                    for (int q = 0; q < I; q++) {
+                        const int gq = mygi[q];
+                        const bool xa = fa[q] && ja != gq, xb = fb[q] && ja + 1 != gq;
+                        const unsigned ma = __ballot_sync(0xffffffffu, xa);
+                        const unsigned mb = __ballot_sync(0xffffffffu, xb);
+                        if (ma | mb) {
+                            const int c0 = mycnt[q];
+                            const unsigned lt = lanemask_lt();
+                            const int pa = c0 + __popc(ma & lt) + __popc(mb & lt);
+                            const int pb = pa + (xa ? 1 : 0);
+                            if ((xa && pa < d.cap) || (xb && pb < d.cap)) {
+                                const int64_t idx = i0 + q;
+                                int32_t *row = d.n_split == 1
+                                                   ? d.list + idx * d.cap
+                                                   : d.plist + (static_cast<int64_t>(sp) * d.n_act + idx) * d.cap;
+                                if (xa && pa < d.cap) row[pa] = ja;
+                                if (xb && pb < d.cap) row[pb] = ja + 1;
+                            }
+                            __syncwarp();
+                            if (lane == 0) mycnt[q] = c0 + __popc(ma) + __popc(mb);
+                            __syncwarp();
+                        }
+                    }
+                }
+            };
+            if (count == JT) {
+#pragma unroll
+                for (int k = 0; k < STEPS; ++k) step(k, false);
+            } else {
+                for (int k = 0; k < STEPS; ++k) step(k, true);
+            }
+
+            // count this warp out of the stage; the last one refills it NST tiles ahead
+            __syncwarp();
+            if (lane == 0) {
+                __threadfence_block();
+                if (atomicAdd(&rel[s], 1) == W - 1) {
+                    rel[s] = 0;
+                    if (la.item < p.n_items) issue_pairs<Fm, JT, NST>(p, la, g + NST, full, stages);
+                }
+            }
+            cursor_next(p, la);
+            if ((t - tb + 1) % FOLD_TILES == 0 || t + 1 == te) {
+#pragma unroll
+                for (int q = 0; q < I; q++) {
+#pragma unroll
+                    for (int c = 0; c < NC; c++) {
+                        f2 &part = c < 3 ? acc[q].f[c] : (c < 6 ? acc[q].j[c - 3] : acc[q].p);
+                        float4 *slot = mytot + (q * NC + c) * 32;
+                        float4 v = *slot;
+                        f2 hi = pk(v.x, v.y), lo = pk(v.z, v.w);
+                        ff_add2(hi, lo, part);
+                        up(hi, v.x, v.y);
+                        up(lo, v.z, v.w);
+                        *slot = v;
+                        part = 0ull;
+                    }
+                }
+            }
+        }
+        if (aborted) break;
+
+        // reduce the float-float totals over both halves and the 32 lanes, then write
+#pragma unroll
+        for (int q = 0; q < I; q++) {
+            double out[7] = {0, 0, 0, 0, 0, 0, 0};
+            for (int c = 0; c < NC; c++) {
+                const float4 v = mytot[(q * NC + c) * 32];
+                float hi = v.x, lo = v.z;
+                ff_add_ff(hi, lo, v.y, v.w);
+                for (int o = 16; o > 0; o >>= 1) {
+                    const float h2 = __shfl_xor_sync(0xffffffffu, hi, o);
+                    const float l2 = __shfl_xor_sync(0xffffffffu, lo, o);
+                    ff_add_ff(hi, lo, h2, l2);
+                }
+                out[c] = static_cast<double>(hi) + static_cast<double>(lo);
+            }
+            const int64_t i = i0 + q;
+            if (lane == 0 && mygi[q] >= 0) {
+                const int cnt = mycnt[q];
+                if (d.n_split == 1) {
+                    for (int c = 0; c < 3; c++) { d.F[3 * i + c] = out[c]; d.J[3 * i + c] = out[3 + c]; }
+                    if (POT && d.pot) d.pot[i] = out[6];
+                    d.nnb[i] = cnt;
+                    d.ovf[i] = cnt > d.cap ? 1 : 0;
+                } else {
+                    double *o8 = d.pF + (static_cast<int64_t>(sp) * d.n_act + i) * 8;
+                    for (int c = 0; c < 7; c++) o8[c] = c < NC ? out[c] : 0.0;
+                    d.pcnt[static_cast<int64_t>(sp) * d.n_act + i] = cnt;
+                }
+            }
+        }
+        __syncwarp();
+    }
+
+    if (aborted && lane == 0) {
+        atomicOr(p.status, DEV_TIMEOUT);
+        for (uint32_t q = g; q < g + NST; ++q) mbar_wait_bounded(&full[q % NST], (q / NST) & 1, p.wait_ns);
+    }
+}
+
+}  // namespace nb

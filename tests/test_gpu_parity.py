@@ -162,12 +162,13 @@ def test_j_range_offset_in_a_larger_context():
 def test_split_and_unsplit_paths_agree():
     w = inputs.cluster(20000, 14, 64, 256, act=np.arange(0, 20000, 97, dtype=np.int32))
     o = oracle_run(w)
-    one = gpu_run(w, "mixed", cfg=B.nb_kcfg(8, 4, 512, 1000))     # one split per i-block
-    many = gpu_run(w, "mixed", cfg=B.nb_kcfg(8, 4, 512, 1))       # one tile per split
-    assert one["launches"] == 1 and many["launches"] == 2
-    for g in (one, many):
-        compare(g, o, w.cap, "mixed")
-    assert np.array_equal(one["list"], many["list"])
+    for packed, jt in ((1, 256), (0, 512)):
+        one = gpu_run(w, "mixed", cfg=B.nb_kcfg(8, 4, jt, 1000, packed))   # one split per i-block
+        many = gpu_run(w, "mixed", cfg=B.nb_kcfg(8, 4, jt, 1, packed))     # one tile per split
+        assert one["launches"] == 1 and many["launches"] == 2
+        for g in (one, many):
+            compare(g, o, w.cap, "mixed")
+        assert np.array_equal(one["list"], many["list"])
 
 
 def _all_cfgs():
@@ -186,7 +187,7 @@ def _all_cfgs():
 def test_every_compiled_configuration(mode, cfg):
     w = inputs.cluster(3100, 15, 40, 128, act=np.arange(0, 3100, 6, dtype=np.int32))
     for split in (0, 1):
-        g = gpu_run(w, mode, cfg=B.nb_kcfg(cfg[0], cfg[1], cfg[2], split))
+        g = gpu_run(w, mode, cfg=B.nb_kcfg(cfg[0], cfg[1], cfg[2], split, cfg[4]))
         assert g["status"] == 0
         compare(g, oracle_run(w), w.cap, mode, lists=(mode != "fp32"))
 
@@ -212,11 +213,16 @@ def _batch(nc=7, seed=40):
     return ws
 
 
-@pytest.mark.parametrize("mode", ["fp64", "mixed"])
-def test_batched_plan_and_graph(mode):
+@pytest.mark.parametrize("mode,even", [("fp64", False), ("mixed", False), ("mixed", True), ("fp32", True)])
+def test_batched_plan_and_graph(mode, even):
+    """Batched plan (one persistent launch + merge) and its CUDA-graph replay.
+    Even slot offsets let the j-pair kernels serve the batch; odd ones take
+    the per-particle layout."""
     import torch
     ws = _batch()
     offs = np.cumsum([0] + [w.n + 13 for w in ws])   # gaps between the clusters' slots
+    if even:
+        offs = offs + (offs % 2)
     with Context(int(offs[-1])) as ctx:
         keep, cl = [], []
         for w, off in zip(ws, offs):
@@ -233,7 +239,7 @@ def test_batched_plan_and_graph(mode):
             assert ctx.sync_status() == 0
             first = [{k: v.cpu().numpy() for k, v in out.items() if v is not None} for _, out in keep]
             for (w, g) in zip(ws, first):
-                compare(g, oracle_run(w), w.cap, mode)
+                compare(g, oracle_run(w), w.cap, mode, lists=(mode != "fp32"))
             for _, out in keep:
                 out["F"].zero_(); out["list"].fill_(-1); out["nnb"].fill_(-5)
             stream = torch.cuda.Stream()
