@@ -76,8 +76,10 @@ typedef struct nb_kcfg {
     int32_t ipw;        /* active particles per warp (the i-tile of a warp)             */
     int32_t jtile;      /* j-particles per shared-memory tile                            */
     int32_t split;      /* j-tiles per work item; 0 = choose from the grid size          */
-    int32_t packed;     /* 1: pair arithmetic of two i-particles per f32x2 instruction
-                         * (float forms); 0: one FP32 or FP64 operation per pair term   */
+    int32_t packed;     /* float forms: 0 = one FP32 operation per pair term; 1 = two
+                         * i-particles per f32x2 instruction; 2 = two j-particles per
+                         * f32x2 instruction (pair-interleaved j-set); 3 = as 2 with two
+                         * j-pairs per lane per step.  FP64 form: 0.                    */
 } nb_kcfg;
 
 /* One independent cluster of a batched call (host struct; the pointers in it

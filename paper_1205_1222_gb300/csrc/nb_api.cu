@@ -220,7 +220,7 @@ nb::JSet jset(const nb_ctx *c, int mode)
 // Streams the j-tiles of kernel entry e are copied from.
 nb::JSet tile_streams(const nb_ctx *c, int mode, const KernelEntry &e)
 {
-    if (e.packed != 2) return jset(c, mode);
+    if (e.packed < 2) return jset(c, mode);
     nb::JSet js{};
     if (mode == NB_MIXED) for (int k = 0; k < 7; k++) js.s[k] = c->pim[k];
     else for (int k = 0; k < 4; k++) js.s[k] = c->pif[k];
@@ -233,7 +233,7 @@ int layout_fallback(int mode, int idx, int flags)
 {
     Registry &r = registry();
     for (size_t i = 0; i < r.all.size(); i++)
-        if (r.all[i].mode == mode && r.all[i].flags == flags && r.all[i].packed != 2) return static_cast<int>(i);
+        if (r.all[i].mode == mode && r.all[i].flags == flags && r.all[i].packed < 2) return static_cast<int>(i);
     return idx;
 }
 
@@ -321,7 +321,7 @@ int run_single(nb_ctx *ctx, const Call &c, const nb_kcfg *cfg_override, cudaStre
     const int flags = (c.dtr ? 1 : 0) | (c.pot ? 2 : 0);
     int idx = find_entry(c.mode, cfg, flags);
     if (idx < 0) { ctx->err = "no kernel for this mode"; return NB_ERR_UNSUPPORTED; }
-    if (registry().all[idx].packed == 2 && (c.j_begin & 1)) idx = layout_fallback(c.mode, idx, flags);
+    if (registry().all[idx].packed >= 2 && (c.j_begin & 1)) idx = layout_fallback(c.mode, idx, flags);
     int occ = 0;
     rc = entry_occupancy(ctx, idx, &occ);
     if (rc != NB_OK) return rc;
@@ -752,7 +752,7 @@ int nb_plan_create(nb_ctx *ctx, int32_t n_clusters, const nb_cluster *cl, int mo
     if (idx < 0) return NB_ERR_UNSUPPORTED;
     bool odd = false;
     for (int c = 0; c < n_clusters; c++) odd |= (cl[c].j_begin & 1) != 0;
-    if (registry().all[idx].packed == 2 && odd) idx = layout_fallback(mode, idx, flags);
+    if (registry().all[idx].packed >= 2 && odd) idx = layout_fallback(mode, idx, flags);
     int occ = 0;
     int rc = entry_occupancy(ctx, idx, &occ);
     if (rc != NB_OK) return rc;

@@ -38,8 +38,9 @@ struct KernelEntry {
     int mode;        // 0 FP64, 1 MIXED, 2 FP32
     int warps, ipw, jtile;
     int flags;       // bit 0: velocity criterion, bit 1: potential
-    int packed;      // 0: scalar kernel (nb_regf.cuh), 1: f32x2 over i-pairs (nb_regf2.cuh),
-                     // 2: f32x2 over j-pairs on the pair-interleaved streams (nb_regf3.cuh)
+    int packed;      // 0: scalar kernel (nb_regf.cuh),
+                     // 2: f32x2 over j-pairs on the pair-interleaved streams (nb_regf3.cuh),
+                     // 3: as 2 with two j-pairs per lane per step
     const void *fn;
     int smem;        // dynamic shared memory bytes
 };

@@ -4,19 +4,13 @@
 namespace nb {
 
 static const KernelEntry g_fp32[] = {
-    NB_KERNEL_ENTRY3(PairFP32, 2, 16, 2, 512, 0, 1),
-    NB_KERNEL_ENTRY3(PairFP32, 2, 12, 2, 512, 1, 1),
-    NB_KERNEL_ENTRY3(PairFP32, 2, 12, 2, 512, 2, 1),
-    NB_KERNEL_ENTRY3(PairFP32, 2, 12, 2, 512, 3, 1),
-    NB_KERNEL_ENTRY3(PairFP32, 2, 12, 2, 512, 0, 1),
-    NB_KERNEL_ENTRY3(PairFP32, 2, 8, 4, 512, 0, 1),
-    NB_KERNEL_ENTRY2(PackedFP32, 2, 12, 4, 256, 0, 1),
-    NB_KERNEL_ENTRY2(PackedFP32, 2, 12, 4, 256, 1, 1),
-    NB_KERNEL_ENTRY2(PackedFP32, 2, 12, 4, 256, 2, 1),
-    NB_KERNEL_ENTRY2(PackedFP32, 2, 12, 4, 256, 3, 1),
-    NB_KERNEL_ENTRY2(PackedFP32, 2, 8, 4, 256, 0, 1),
-    NB_KERNEL_ENTRY2(PackedFP32, 2, 16, 2, 256, 0, 1),
-    NB_KERNEL_ENTRY2(PackedFP32, 2, 8, 2, 256, 0, 2),
+    NB_KERNEL_ENTRY3(PairFP32, 2, 16, 2, 512, 4, 1, 0, 1),
+    NB_KERNEL_ENTRY3(PairFP32, 2, 16, 2, 512, 4, 1, 1, 1),
+    NB_KERNEL_ENTRY3(PairFP32, 2, 16, 2, 512, 4, 1, 2, 1),
+    NB_KERNEL_ENTRY3(PairFP32, 2, 16, 2, 512, 4, 1, 3, 1),
+    NB_KERNEL_ENTRY3(PairFP32, 2, 16, 2, 512, 6, 2, 0, 1),
+    NB_KERNEL_ENTRY3(PairFP32, 2, 8, 2, 256, 6, 1, 0, 2),
+    NB_KERNEL_ENTRY3(PairFP32, 2, 8, 4, 512, 4, 1, 0, 1),
     NB_KERNEL_ENTRY(FormFP32, 2, 8, 4, 512, 0),
     NB_KERNEL_ENTRY(FormFP32, 2, 8, 8, 512, 0),
     NB_KERNEL_ENTRY(FormFP32, 2, 8, 2, 512, 0),

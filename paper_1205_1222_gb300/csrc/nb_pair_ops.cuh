@@ -1,0 +1,170 @@
+// f32x2 building blocks of the packed regular-force kernel (nb_regf3.cuh):
+// Blackwell's add/sub/mul/fma.rn.f32x2 on two FP32 values held in a 64-bit
+// register pair, the shared pair-term tail (r^2, R.V, neighbour test of
+// Sec. 3.2, 1/r, force and jerk of Sec. 3.3 step (vi)), and the cursor that
+// walks a CTA's sequence of j-tiles across work items.
+#pragma once
+
+#include <cfloat>
+
+#include "nb_device.cuh"
+#include "nb_regf.cuh"
+
+namespace nb {
+
+typedef unsigned long long f2;   // two FP32 values in a 64-bit register pair (.x = first of the pair)
+
+__device__ __forceinline__ f2 pk(float a, float b)
+{
+    f2 r;
+    asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(a), "f"(b));
+    return r;
+}
+__device__ __forceinline__ f2 bc(float a) { return pk(a, a); }
+__device__ __forceinline__ void up(f2 v, float &a, float &b)
+{
+    asm("mov.b64 {%0, %1}, %2;" : "=f"(a), "=f"(b) : "l"(v));
+}
+__device__ __forceinline__ f2 add2(f2 a, f2 b)
+{
+    f2 d;
+    asm("add.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+    return d;
+}
+__device__ __forceinline__ f2 sub2(f2 a, f2 b)
+{
+    f2 d;
+    asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+    return d;
+}
+__device__ __forceinline__ f2 mul2(f2 a, f2 b)
+{
+    f2 d;
+    asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+    return d;
+}
+__device__ __forceinline__ f2 fma2(f2 a, f2 b, f2 c)
+{
+    f2 d;
+    asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(d) : "l"(a), "l"(b), "l"(c));
+    return d;
+}
+// Hardware reciprocal square root approximation (PTX rsqrt.approx; a zero
+// argument gives +inf, which the neighbour select replaces by 0 for self).
+__device__ __forceinline__ float rsqrt_hw(float x)
+{
+    float y;
+    asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+
+struct Acc2 {
+    f2 f[3], j[3], p;
+};
+
+// Shared tail of the packed pair terms: r^2, R.V, neighbour test, 1/r, force,
+// jerk (and potential) for an i-pair against one j.
+template <bool VC, bool POT>
+__device__ __forceinline__ void tail2(f2 h2, f2 dtr, f2 m, f2 dx, f2 dy, f2 dz, f2 ux, f2 uy, f2 uz,
+                                      Acc2 &a, bool &fa, bool &fb)
+{
+    const f2 r2 = fma2(dz, dz, fma2(dy, dy, mul2(dx, dx)));
+    const f2 rv = fma2(dz, uz, fma2(dy, uy, mul2(dx, ux)));
+    float r2a, r2b, qa, qb, ha, hb;
+    up(r2, r2a, r2b);
+    qa = r2a;
+    qb = r2b;
+    if (VC) {
+        const f2 px = fma2(dtr, ux, dx), py = fma2(dtr, uy, dy), pz = fma2(dtr, uz, dz);
+        float pa, pb;
+        up(fma2(pz, pz, fma2(py, py, mul2(px, px))), pa, pb);
+        qa = fminf(qa, pa);
+        qb = fminf(qb, pb);
+    }
+    up(h2, ha, hb);
+    fa = qa < ha;
+    fb = qb < hb;
+    float ra = rsqrt_hw(r2a), rb = rsqrt_hw(r2b);
+    ra = fa ? 0.f : ra;
+    rb = fb ? 0.f : rb;
+    const f2 rinv = pk(ra, rb);
+    const f2 rinv2 = mul2(rinv, rinv);
+    const f2 mr = mul2(m, rinv);
+    const f2 mr3 = mul2(mr, rinv2);
+    const f2 al = mul2(bc(-3.f), mul2(rv, rinv2));
+    a.f[0] = fma2(mr3, dx, a.f[0]);
+    a.f[1] = fma2(mr3, dy, a.f[1]);
+    a.f[2] = fma2(mr3, dz, a.f[2]);
+    a.j[0] = fma2(mr3, fma2(al, dx, ux), a.j[0]);
+    a.j[1] = fma2(mr3, fma2(al, dy, uy), a.j[1]);
+    a.j[2] = fma2(mr3, fma2(al, dz, uz), a.j[2]);
+    if (POT) a.p = add2(a.p, mr);
+}
+
+// As tail2, but returns only whether either half is a neighbour; the j-pair
+// kernels recompute the individual tests (test2) on the rare steps that have
+// one, with the same operations, so fewer predicates stay live.
+template <bool VC, bool POT>
+__device__ __forceinline__ bool tail2_any(f2 h2, f2 dtr, f2 m, f2 dx, f2 dy, f2 dz, f2 ux, f2 uy, f2 uz, Acc2 &a)
+{
+    bool fa, fb;
+    tail2<VC, POT>(h2, dtr, m, dx, dy, dz, ux, uy, uz, a, fa, fb);
+    return fa | fb;
+}
+
+// The neighbour test of tail2 alone (same operations, so the same decisions).
+template <bool VC>
+__device__ __forceinline__ void test2(f2 h2, f2 dtr, f2 dx, f2 dy, f2 dz, f2 ux, f2 uy, f2 uz, bool &fa, bool &fb)
+{
+    const f2 r2 = fma2(dz, dz, fma2(dy, dy, mul2(dx, dx)));
+    float qa, qb, ha, hb;
+    up(r2, qa, qb);
+    if (VC) {
+        const f2 px = fma2(dtr, ux, dx), py = fma2(dtr, uy, dy), pz = fma2(dtr, uz, dz);
+        float pa, pb;
+        up(fma2(pz, pz, fma2(py, py, mul2(px, px))), pa, pb);
+        qa = fminf(qa, pa);
+        qb = fminf(qb, pb);
+    }
+    up(h2, ha, hb);
+    fa = qa < ha;
+    fb = qb < hb;
+}
+
+// Position in the CTA's sequence of j-tiles: the work item, the tile in it,
+// the item's tile end, and the j-range the copies read.
+struct TileCursor {
+    int64_t item;
+    int64_t jb;
+    int nj, tile, te;
+};
+
+__device__ __forceinline__ void cursor_set(const RegfParams &p, TileCursor &c)
+{
+    if (c.item >= p.n_items) return;
+    int64_t item_begin, jb;
+    int n_split, tps, n_tiles, nj;
+    if (p.table) {
+        const ClusterDesc &d = p.table[find_cluster(p, c.item)];
+        item_begin = d.item_begin; jb = d.j_begin; nj = d.n_j;
+        n_split = d.n_split; tps = d.tiles_per_split; n_tiles = d.n_tiles;
+    } else {
+        item_begin = p.d0.item_begin; jb = p.d0.j_begin; nj = p.d0.n_j;
+        n_split = p.d0.n_split; tps = p.d0.tiles_per_split; n_tiles = p.d0.n_tiles;
+    }
+    const int64_t local = c.item - item_begin;
+    const int sp = static_cast<int>(local % n_split);
+    c.jb = jb;
+    c.nj = nj;
+    c.tile = sp * tps;
+    c.te = min(c.tile + tps, n_tiles);
+}
+
+__device__ __forceinline__ void cursor_next(const RegfParams &p, TileCursor &c)
+{
+    if (++c.tile < c.te) return;
+    c.item += gridDim.x;
+    cursor_set(p, c);
+}
+
+}  // namespace nb

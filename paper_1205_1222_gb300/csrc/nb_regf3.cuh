@@ -9,15 +9,24 @@
 // j-pair P (slots 2P, 2P+1) stream k holds one float4 with two components of
 // both particles, e.g. (x_a, x_b, y_a, y_b), so one 128-bit shared-memory
 // load yields two ready register pairs and no lane ever moves a value into a
-// pair.  Everything else follows nb_regf2.cuh: the NST-stage TMA ring
-// released by the last warp out, float-float totals in shared memory,
-// ballot + popc list compaction (here over the interleaved (lane, half)
-// order, which is ascending j).
+// pair.  The j-tiles flow through an NSTAGE-deep TMA ring without CTA-wide
+// barriers: each warp waits on the stage's full mbarrier, computes, and counts
+// itself out of the stage on a shared counter; the last warp out refills the
+// stage with the tile NSTAGE steps ahead (every warp tracks that look-ahead
+// position), so warps drift freely within the ring.  Per-lane float-float
+// totals live in shared memory (folded every FOLD_STEPS steps), leaving the
+// register file to the i-values and the FP32 partial sums.  The pair terms of
+// a tile run as straight-line code that only marks, per i-particle, which
+// 64-j units held a neighbour; after the tile the lists are compacted from the
+// marked units with ballot + popc over the interleaved (lane, half) order,
+// which is ascending j, the neighbour test being recomputed by the same
+// operations.
 #pragma once
 
 #include <cfloat>
+#include <type_traits>
 
-#include "nb_regf2.cuh"
+#include "nb_pair_ops.cuh"
 
 namespace nb {
 
@@ -74,16 +83,29 @@ struct PairMixed {
         ib.h2 = bc(h2);
         ib.dtr = bc(dtr);
     }
-    template <bool VC, bool POT>
-    static __device__ __forceinline__ void pair(const IB &i, const JP &j, Acc2 &a, bool &fa, bool &fb)
+    static __device__ __forceinline__ void diffs(const IB &i, const JP &j, f2 &dx, f2 &dy, f2 &dz, f2 &ux, f2 &uy,
+                                                 f2 &uz)
     {
-        const f2 dx = add2(add2(j.xh[0], i.nxh[0]), add2(j.xl[0], i.nxl[0]));
-        const f2 dy = add2(add2(j.xh[1], i.nxh[1]), add2(j.xl[1], i.nxl[1]));
-        const f2 dz = add2(add2(j.xh[2], i.nxh[2]), add2(j.xl[2], i.nxl[2]));
-        const f2 ux = add2(add2(j.vh[0], i.nvh[0]), add2(j.vl[0], i.nvl[0]));
-        const f2 uy = add2(add2(j.vh[1], i.nvh[1]), add2(j.vl[1], i.nvl[1]));
-        const f2 uz = add2(add2(j.vh[2], i.nvh[2]), add2(j.vl[2], i.nvl[2]));
-        tail2<VC, POT>(i.h2, i.dtr, j.m, dx, dy, dz, ux, uy, uz, a, fa, fb);
+        dx = add2(add2(j.xh[0], i.nxh[0]), add2(j.xl[0], i.nxl[0]));
+        dy = add2(add2(j.xh[1], i.nxh[1]), add2(j.xl[1], i.nxl[1]));
+        dz = add2(add2(j.xh[2], i.nxh[2]), add2(j.xl[2], i.nxl[2]));
+        ux = add2(add2(j.vh[0], i.nvh[0]), add2(j.vl[0], i.nvl[0]));
+        uy = add2(add2(j.vh[1], i.nvh[1]), add2(j.vl[1], i.nvl[1]));
+        uz = add2(add2(j.vh[2], i.nvh[2]), add2(j.vl[2], i.nvl[2]));
+    }
+    template <bool VC, bool POT>
+    static __device__ __forceinline__ bool pair(const IB &i, const JP &j, Acc2 &a)
+    {
+        f2 dx, dy, dz, ux, uy, uz;
+        diffs(i, j, dx, dy, dz, ux, uy, uz);
+        return tail2_any<VC, POT>(i.h2, i.dtr, j.m, dx, dy, dz, ux, uy, uz, a);
+    }
+    template <bool VC>
+    static __device__ __forceinline__ void test(const IB &i, const JP &j, bool &fa, bool &fb)
+    {
+        f2 dx, dy, dz, ux, uy, uz;
+        diffs(i, j, dx, dy, dz, ux, uy, uz);
+        test2<VC>(i.h2, i.dtr, dx, dy, dz, ux, uy, uz, fa, fb);
     }
 };
 
@@ -131,21 +153,29 @@ struct PairFP32 {
         ib.dtr = bc(dtr);
     }
     template <bool VC, bool POT>
-    static __device__ __forceinline__ void pair(const IB &i, const JP &j, Acc2 &a, bool &fa, bool &fb)
+    static __device__ __forceinline__ bool pair(const IB &i, const JP &j, Acc2 &a)
     {
-        tail2<VC, POT>(i.h2, i.dtr, j.m, add2(j.x[0], i.nx[0]), add2(j.x[1], i.nx[1]), add2(j.x[2], i.nx[2]),
-                       add2(j.v[0], i.nv[0]), add2(j.v[1], i.nv[1]), add2(j.v[2], i.nv[2]), a, fa, fb);
+        return tail2_any<VC, POT>(i.h2, i.dtr, j.m, add2(j.x[0], i.nx[0]), add2(j.x[1], i.nx[1]),
+                                  add2(j.x[2], i.nx[2]), add2(j.v[0], i.nv[0]), add2(j.v[1], i.nv[1]),
+                                  add2(j.v[2], i.nv[2]), a);
+    }
+    template <bool VC>
+    static __device__ __forceinline__ void test(const IB &i, const JP &j, bool &fa, bool &fb)
+    {
+        test2<VC>(i.h2, i.dtr, add2(j.x[0], i.nx[0]), add2(j.x[1], i.nx[1]), add2(j.x[2], i.nx[2]),
+                  add2(j.v[0], i.nv[0]), add2(j.v[1], i.nv[1]), add2(j.v[2], i.nv[2]), fa, fb);
     }
 };
 
-template <class Fm, int W, int I, int JT>
+template <class Fm, int W, int I, int JT, int NST_>
 struct PairLayout {
-    static constexpr int NST = 4;                                  // stages of the j-tile ring
+    static constexpr int NST = NST_;                               // stages of the j-tile ring
     static constexpr int NP = JT / 2;                              // j-pairs per tile
     static constexpr int STAGE = Fm::NS * 16 * NP;
     static constexpr int STAGES = 128;                             // barriers + release counters first
     static constexpr int TOT = STAGES + NST * STAGE;
-    __host__ __device__ static constexpr int tot_bytes(bool pot) { return W * I * (pot ? 7 : 6) * 32 * 16; }
+    // float-float totals: one (hi, lo) float2 per (warp, i, component, lane)
+    __host__ __device__ static constexpr int tot_bytes(bool pot) { return W * I * (pot ? 7 : 6) * 32 * 8; }
     __host__ __device__ static constexpr int cnt(bool pot) { return TOT + tot_bytes(pot); }
     __host__ __device__ static constexpr int gi(bool pot) { return cnt(pot) + W * I * 4; }
     __host__ __device__ static constexpr int desc(bool pot) { return gi(pot) + W * I * 4; }
@@ -155,10 +185,10 @@ struct PairLayout {
     }
 };
 
-template <class Fm, int W, int I, int JT>
+template <class Fm, int W, int I, int JT, int NST>
 constexpr int pair_smem_bytes(bool pot)
 {
-    return PairLayout<Fm, W, I, JT>::bytes(pot);
+    return PairLayout<Fm, W, I, JT, NST>::bytes(pot);
 }
 
 // Copy the pair-interleaved tile at cursor c into ring slot seq % NST.  The
@@ -182,10 +212,12 @@ __device__ __forceinline__ void issue_pairs(const RegfParams &p, const TileCurso
         tma_bulk_g2s(st + k * NP * 16, static_cast<const unsigned char *>(p.js.s[k]) + first * 16, bytes, b);
 }
 
-template <class Fm, int W, int I, int JT, int FLAGS, int MINB>
+template <class Fm, int W, int I, int JT, int NSTAGE, int U, int FLAGS, int MINB>
 __global__ void __launch_bounds__(W * 32, MINB) regf3_kernel(const RegfParams p)
 {
-    using L = PairLayout<Fm, W, I, JT>;
+    static_assert(NSTAGE <= 12, "ring barriers and release counters share the first 128 bytes");
+    static_assert((JT / 64) % U == 0, "a tile holds a whole number of steps");
+    using L = PairLayout<Fm, W, I, JT, NSTAGE>;
     constexpr bool VC = (FLAGS & 1) != 0;
     constexpr bool POT = (FLAGS & 2) != 0;
     constexpr int NC = POT ? 7 : 6;
@@ -201,7 +233,7 @@ __global__ void __launch_bounds__(W * 32, MINB) regf3_kernel(const RegfParams p)
     uint64_t *full = reinterpret_cast<uint64_t *>(smem);
     int *rel = reinterpret_cast<int *>(smem + 8 * NST);
     unsigned char *stages = smem + L::STAGES;
-    float4 *s_tot = reinterpret_cast<float4 *>(smem + L::TOT);
+    float2 *s_tot = reinterpret_cast<float2 *>(smem + L::TOT);
     int *s_cnt = reinterpret_cast<int *>(smem + L::cnt(POT));
     int *s_gi = reinterpret_cast<int *>(smem + L::gi(POT));
     ClusterDesc *s_d = reinterpret_cast<ClusterDesc *>(smem + L::desc(POT));
@@ -227,7 +259,7 @@ __global__ void __launch_bounds__(W * 32, MINB) regf3_kernel(const RegfParams p)
 
     uint32_t g = 0;
     bool aborted = false;
-    float4 *mytot = s_tot + warp * I * NC * 32 + lane;   // + (i * NC + comp) * 32: (hi_a, hi_b, lo_a, lo_b)
+    float2 *mytot = s_tot + warp * I * NC * 32 + lane;   // + (i * NC + comp) * 32: (hi, lo)
     int *mycnt = s_cnt + warp * I;
     int *mygi = s_gi + warp * I;
     ClusterDesc &d = s_d[warp];
@@ -266,7 +298,7 @@ __global__ void __launch_bounds__(W * 32, MINB) regf3_kernel(const RegfParams p)
             Fm::set_i(ipart[k], p.soa, slot, h2v, dtv);
             for (int c = 0; c < 3; c++) acc[k].f[c] = acc[k].j[c] = 0ull;
             acc[k].p = 0ull;
-            for (int c = 0; c < NC; c++) mytot[(k * NC + c) * 32] = make_float4(0.f, 0.f, 0.f, 0.f);
+            for (int c = 0; c < NC; c++) mytot[(k * NC + c) * 32] = make_float2(0.f, 0.f);
         }
         __syncwarp();
 
@@ -277,51 +309,67 @@ __global__ void __launch_bounds__(W * 32, MINB) regf3_kernel(const RegfParams p)
             const int jt0 = t * JT;
             const int count = min(JT, d.n_j - jt0);
 
-            auto step = [&](int k, bool tail) {
-                const int pl = k * 32 + lane;
-                JP jp;
-                Fm::template load_j<NP>(jp, st, pl);
-                if (tail) Fm::mask(jp, 2 * pl < count, 2 * pl + 1 < count);
-                bool fa[I], fb[I];
-                bool any = false;
+            // Pair terms of the whole tile: U j-pairs per lane per step (U * 64
+            // consecutive j for the warp), no branch; a neighbour in unit
+            // (pair-step k*U+u, i-particle q) only sets bit k*U+u of bits[q].
+            uint32_t bits[I];
 #pragma unroll
-                for (int q = 0; q < I; q++) {
-                    Fm::template pair<VC, POT>(ipart[q], jp, acc[q], fa[q], fb[q]);
-                    any |= fa[q] | fb[q];
-                }
-                if (__any_sync(0xffffffffu, any)) {
-                    const int ja = jt0 + 2 * pl;
+            for (int q = 0; q < I; q++) bits[q] = 0u;
+            auto step = [&](int k, auto tail_c) {
+                constexpr bool tail = decltype(tail_c)::value;
 #pragma unroll
-                    for (int q = 0; q < I; q++) {
-                        const int gq = mygi[q];
-                        const bool xa = fa[q] && ja != gq, xb = fb[q] && ja + 1 != gq;
-                        const unsigned ma = __ballot_sync(0xffffffffu, xa);
-                        const unsigned mb = __ballot_sync(0xffffffffu, xb);
-                        if (ma | mb) {
-                            const int c0 = mycnt[q];
-                            const unsigned lt = lanemask_lt();
-                            const int pa = c0 + __popc(ma & lt) + __popc(mb & lt);
-                            const int pb = pa + (xa ? 1 : 0);
-                            if ((xa && pa < d.cap) || (xb && pb < d.cap)) {
-                                const int64_t idx = i0 + q;
-                                int32_t *row = d.n_split == 1
-                                                   ? d.list + idx * d.cap
-                                                   : d.plist + (static_cast<int64_t>(sp) * d.n_act + idx) * d.cap;
-                                if (xa && pa < d.cap) row[pa] = ja;
-                                if (xb && pb < d.cap) row[pb] = ja + 1;
-                            }
-                            __syncwarp();
-                            if (lane == 0) mycnt[q] = c0 + __popc(ma) + __popc(mb);
-                            __syncwarp();
-                        }
-                    }
+                for (int u = 0; u < U; u++) {
+                    const int pl = (k * U + u) * 32 + lane;
+                    JP jp;
+                    Fm::template load_j<NP>(jp, st, pl);
+                    if (tail) Fm::mask(jp, 2 * pl < count, 2 * pl + 1 < count);
+#pragma unroll
+                    for (int q = 0; q < I; q++)
+                        if (Fm::template pair<VC, POT>(ipart[q], jp, acc[q])) bits[q] |= 1u << (k * U + u);
                 }
             };
             if (count == JT) {
 #pragma unroll
-                for (int k = 0; k < STEPS; ++k) step(k, false);
+                for (int k = 0; k < STEPS / U; ++k) step(k, std::false_type{});
             } else {
-                for (int k = 0; k < STEPS; ++k) step(k, true);
+#pragma unroll 1
+                for (int k = 0; k < STEPS / U; ++k) step(k, std::true_type{});
+            }
+            // Neighbour lists of the tile, in ascending j: for each i-particle,
+            // the flagged units in order; within a unit the order is (lane, half).
+#pragma unroll
+            for (int q = 0; q < I; q++) {
+                uint32_t todo = __reduce_or_sync(0xffffffffu, bits[q]);
+                while (todo) {
+                    const int unit = __ffs(todo) - 1;
+                    todo &= todo - 1;
+                    const int pl = unit * 32 + lane;
+                    JP jp;
+                    Fm::template load_j<NP>(jp, st, pl);
+                    if (count < JT) Fm::mask(jp, 2 * pl < count, 2 * pl + 1 < count);
+                    bool fa, fb;
+                    Fm::template test<VC>(ipart[q], jp, fa, fb);
+                    const int ja = jt0 + 2 * pl;
+                    const int gq = mygi[q];
+                    const bool xa = fa && ja != gq, xb = fb && ja + 1 != gq;
+                    const unsigned ma = __ballot_sync(0xffffffffu, xa);
+                    const unsigned mb = __ballot_sync(0xffffffffu, xb);
+                    const int c0 = mycnt[q];
+                    const unsigned lt = lanemask_lt();
+                    const int pa = c0 + __popc(ma & lt) + __popc(mb & lt);
+                    const int pb = pa + (xa ? 1 : 0);
+                    if ((xa && pa < d.cap) || (xb && pb < d.cap)) {
+                        const int64_t idx = i0 + q;
+                        int32_t *row = d.n_split == 1
+                                           ? d.list + idx * d.cap
+                                           : d.plist + (static_cast<int64_t>(sp) * d.n_act + idx) * d.cap;
+                        if (xa && pa < d.cap) row[pa] = ja;
+                        if (xb && pb < d.cap) row[pb] = ja + 1;
+                    }
+                    __syncwarp();
+                    if (lane == 0) mycnt[q] = c0 + __popc(ma) + __popc(mb);
+                    __syncwarp();
+                }
             }
 
             // count this warp out of the stage; the last one refills it NST tiles ahead
@@ -340,12 +388,11 @@ __global__ void __launch_bounds__(W * 32, MINB) regf3_kernel(const RegfParams p)
 #pragma unroll
                     for (int c = 0; c < NC; c++) {
                         f2 &part = c < 3 ? acc[q].f[c] : (c < 6 ? acc[q].j[c - 3] : acc[q].p);
-                        float4 *slot = mytot + (q * NC + c) * 32;
-                        float4 v = *slot;
-                        f2 hi = pk(v.x, v.y), lo = pk(v.z, v.w);
-                        ff_add2(hi, lo, part);
-                        up(hi, v.x, v.y);
-                        up(lo, v.z, v.w);
+                        float2 *slot = mytot + (q * NC + c) * 32;
+                        float2 v = *slot;
+                        float pa, pb;
+                        up(part, pa, pb);
+                        ff_add(v.x, v.y, pa + pb);   // the two halves' partials first, then TwoSum
                         *slot = v;
                         part = 0ull;
                     }
@@ -359,9 +406,8 @@ __global__ void __launch_bounds__(W * 32, MINB) regf3_kernel(const RegfParams p)
         for (int q = 0; q < I; q++) {
             double out[7] = {0, 0, 0, 0, 0, 0, 0};
             for (int c = 0; c < NC; c++) {
-                const float4 v = mytot[(q * NC + c) * 32];
-                float hi = v.x, lo = v.z;
-                ff_add_ff(hi, lo, v.y, v.w);
+                const float2 v = mytot[(q * NC + c) * 32];
+                float hi = v.x, lo = v.y;
                 for (int o = 16; o > 0; o >>= 1) {
                     const float h2 = __shfl_xor_sync(0xffffffffu, hi, o);
                     const float l2 = __shfl_xor_sync(0xffffffffu, lo, o);

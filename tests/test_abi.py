@@ -42,8 +42,9 @@ def test_library_loads_and_answers_host_queries(lib_path):
         assert n >= 1
         cfgs = [binding.nb_get_kernel_config(mode, i).as_tuple() for i in range(n)]
         assert len(set(cfgs)) == n
-        for w, ipw, jt, split in cfgs:
+        for w, ipw, jt, split, packed in cfgs:
             assert w > 0 and ipw > 0 and jt % 32 == 0 and split == 0
+            assert packed in ((0,) if mode == binding.NB_FP64 else (0, 2, 3))
     assert lib.nb_create is not None
 
 
