@@ -162,9 +162,9 @@ def test_j_range_offset_in_a_larger_context():
 def test_split_and_unsplit_paths_agree():
     w = inputs.cluster(20000, 14, 64, 256, act=np.arange(0, 20000, 97, dtype=np.int32))
     o = oracle_run(w)
-    for packed, jt in ((1, 256), (0, 512)):
-        one = gpu_run(w, "mixed", cfg=B.nb_kcfg(8, 4, jt, 1000, packed))   # one split per i-block
-        many = gpu_run(w, "mixed", cfg=B.nb_kcfg(8, 4, jt, 1, packed))     # one tile per split
+    for warps, ipw, jt, packed in ((16, 2, 512, 2), (8, 4, 512, 0)):
+        one = gpu_run(w, "mixed", cfg=B.nb_kcfg(warps, ipw, jt, 1000, packed))   # one split per i-block
+        many = gpu_run(w, "mixed", cfg=B.nb_kcfg(warps, ipw, jt, 1, packed))     # one tile per split
         assert one["launches"] == 1 and many["launches"] == 2
         for g in (one, many):
             compare(g, o, w.cap, "mixed")
