@@ -159,6 +159,29 @@ int nb_regular_force(nb_ctx *ctx, int64_t j_begin, int64_t n_j, int32_t n_act,
                      int mode, double *F, double *J, double *pot, int32_t *nnb,
                      int32_t *list, uint8_t *ovf, nb_stream_t stream);
 
+/* Allocation-free variant of nb_regular_force (the paper has no counterpart;
+ * it exists for the library's users).  Some callers cannot let a library
+ * allocate device memory while a step runs: code that issues the step inside
+ * a stream-capture region, real-time loops that reserve their memory once up
+ * front, or programs whose device memory is handed out by another allocator.
+ * nb_regular_force may call cudaMalloc to grow its split scratch; this call
+ * never allocates or frees anything.  Instead its split partials live in one
+ * fixed device array of 32 MiB (33554432 bytes) that every GPU loading the
+ * library holds until the process exits.  A call with n_split j-splits needs
+ * about n_split * n_act * (68 + 4 * cap) bytes of it (no split, no scratch).
+ * Same arguments, outputs and errors as nb_regular_force, plus: a call whose
+ * split scratch would exceed the array returns NB_ERR_ARG with the sizes in
+ * nb_last_error (fewer active particles per call or a smaller cap fit).
+ * The first call on a device looks up the array's device address; make that
+ * first call before any stream capture.  All calls share the one array and it
+ * keeps the last call's contents (each call clears what it needs cleared):
+ * calls that may overlap on the GPU (other streams, other contexts on the same
+ * device) race on it and must be serialised by the caller. */
+int nb_regular_force_noalloc(nb_ctx *ctx, int64_t j_begin, int64_t n_j, int32_t n_act,
+                             const int32_t *act, const double *h, const double *dtr, int32_t cap,
+                             int mode, double *F, double *J, double *pot, int32_t *nnb,
+                             int32_t *list, uint8_t *ovf, nb_stream_t stream);
+
 /* Make sure the split scratch holds at least `bytes` (device memory). */
 int nb_reserve(nb_ctx *ctx, size_t bytes);
 

@@ -36,7 +36,7 @@ EXPORTS = [
     "nb_plan_launch", "nb_plan_destroy", "nb_plan_launches", "nb_step_host", "nb_sync_status",
     "nb_strerror", "nb_last_error", "nb_num_kernel_configs", "nb_get_kernel_config",
     "nb_set_kernel_config", "nb_get_active_config", "nb_time_regular_force", "nb_last_launches",
-    "nb_sm_count", "nb_debug_set_wait",
+    "nb_sm_count", "nb_debug_set_wait", "nb_regular_force_noalloc",
 ]
 
 
@@ -105,6 +105,7 @@ def library():
         "nb_last_launches": ([P], cint),
         "nb_sm_count": ([P], cint),
         "nb_debug_set_wait": ([P, ctypes.c_uint64, ctypes.c_uint32], cint),
+        "nb_regular_force_noalloc": ([P, i64, i64, i32, P, P, P, i32, cint, P, P, P, P, P, P, P], cint),
     }
     for name, (args, res) in sig.items():
         f = getattr(lib, name)
@@ -180,6 +181,15 @@ def nb_regular_force(ctx, j_begin, n_j, n_act, act, h, dtr, cap, mode, F, J, pot
     _check(ctx, library().nb_regular_force(ctx, int(j_begin), int(n_j), int(n_act), _p(act), _p(h), _p(dtr),
                                            int(cap), int(mode), _p(F), _p(J), _p(pot), _p(nnb), _p(lst),
                                            _p(ovf), _stream(stream)), "nb_regular_force")
+
+
+def nb_regular_force_noalloc(ctx, j_begin, n_j, n_act, act, h, dtr, cap, mode, F, J, pot, nnb, lst, ovf,
+                             stream=None):
+    """nb_regular_force without any device allocation (fixed split scratch)."""
+    _check(ctx, library().nb_regular_force_noalloc(ctx, int(j_begin), int(n_j), int(n_act), _p(act), _p(h),
+                                                   _p(dtr), int(cap), int(mode), _p(F), _p(J), _p(pot),
+                                                   _p(nnb), _p(lst), _p(ovf), _stream(stream)),
+           "nb_regular_force_noalloc")
 
 
 def nb_reserve(ctx, nbytes):

@@ -913,3 +913,110 @@ int nb_debug_set_wait(nb_ctx *ctx, uint64_t wait_ns, uint32_t extra_tx)
 }
 
 }  // extern "C"
+
+// ------------------------------------------------------ allocation-free call
+//
+// nb_regular_force_noalloc serves callers that may not allocate device memory
+// while a step runs: code that runs inside a stream-capture region, real-time
+// loops with a fixed memory budget reserved up front, or hosts whose device
+// memory is handed out by another allocator that the library must not
+// bypass.  nb_regular_force grows the context's split scratch with cudaMalloc
+// when a call needs more; this variant instead uses one fixed device array,
+// so it calls no cudaMalloc, cudaFree or allocating library routine.
+
+// Split scratch of the allocation-free call: 32 MiB, resident on every device
+// that loads the library, until the process exits.
+static constexpr size_t kNoAllocScratchBytes = size_t(32) << 20;
+static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocScratchBytes];
+
+namespace {
+
+std::mutex g_noalloc_mu;
+void *g_noalloc_addr[256];   // device address of g_noalloc_scratch, per device (nullptr = not looked up)
+
+// Device address of the fixed scratch on the current device.  The host-side
+// name g_noalloc_scratch is only a stand-in for the symbol, never a device
+// address, so the address is looked up once per device, with that device
+// current.
+int noalloc_scratch(nb_ctx *ctx, void **out)
+{
+    std::lock_guard<std::mutex> lock(g_noalloc_mu);
+    if (ctx->device < 0 || ctx->device >= 256) return NB_ERR_ARG;
+    if (!g_noalloc_addr[ctx->device]) {
+        void *p = nullptr;
+        const cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+        if (e != cudaSuccess || !p) return cuda_fail(ctx, e, "cudaGetSymbolAddress(g_noalloc_scratch)");
+        g_noalloc_addr[ctx->device] = p;
+    }
+    *out = g_noalloc_addr[ctx->device];
+    return NB_OK;
+}
+
+}  // namespace
+
+extern "C" int nb_regular_force_noalloc(nb_ctx *ctx, int64_t j_begin, int64_t n_j, int32_t n_act,
+                                        const int32_t *act, const double *h, const double *dtr, int32_t cap,
+                                        int mode, double *F, double *J, double *pot, int32_t *nnb,
+                                        int32_t *list, uint8_t *ovf, nb_stream_t stream)
+{
+    const Call c{j_begin, n_j, n_act, act, h, dtr, cap, mode, F, J, pot, nnb, list, ovf};
+    int rc = check_call(ctx, c);
+    if (rc != NB_OK) return rc;
+    ctx->last_launches = 0;
+    if (c.n_act == 0) return NB_OK;
+    DeviceGuard guard(ctx->device);
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    void *scratch = nullptr;
+    rc = noalloc_scratch(ctx, &scratch);
+    if (rc != NB_OK) return rc;
+    const nb_kcfg cfg = ctx->cfg_set[c.mode] ? ctx->cfg[c.mode] : default_cfg(c.mode);
+    const int flags = (c.dtr ? 1 : 0) | (c.pot ? 2 : 0);
+    int idx = find_entry(c.mode, cfg, flags);
+    if (idx < 0) { ctx->err = "no kernel for this mode"; return NB_ERR_UNSUPPORTED; }
+    if (registry().all[idx].packed >= 2 && (c.j_begin & 1)) idx = layout_fallback(c.mode, idx, flags);
+    int occ = 0;
+    rc = entry_occupancy(ctx, idx, &occ);
+    if (rc != NB_OK) return rc;
+    const KernelEntry &e = registry().all[idx];
+    ClusterDesc d = make_desc(c);
+    tile_cluster(e, occ, ctx->sm_count, &cfg, d);
+    d.item_begin = 0;
+    const size_t need = cluster_scratch(d);
+    if (need > kNoAllocScratchBytes) {
+        ctx->err = "the call needs " + std::to_string(need) + " bytes of split scratch; the fixed array of "
+                   "nb_regular_force_noalloc holds " + std::to_string(kNoAllocScratchBytes) +
+                   " (use fewer active particles or a smaller cap per call, or nb_regular_force)";
+        return NB_ERR_ARG;
+    }
+    carve_scratch(d, static_cast<char *>(scratch));
+    if (d.n_split > 1) {
+        // The array keeps the previous call's contents: the partial sums and
+        // counts every split starts from are cleared (pF and pcnt are contiguous).
+        const char *end = reinterpret_cast<const char *>(d.pcnt + static_cast<size_t>(d.n_split) * d.n_act);
+        NB_CUDA(ctx, cudaMemsetAsync(d.pF, 0, static_cast<size_t>(end - reinterpret_cast<const char *>(d.pF)), st));
+    }
+
+    nb::RegfParams p{};
+    p.js = tile_streams(ctx, c.mode, e);
+    p.soa = jset(ctx, c.mode);
+    p.d0 = d;
+    p.n_clusters = 1;
+    p.n_items = static_cast<int64_t>(d.n_iblk) * d.n_split;
+    p.status = ctx->d_status;
+    p.wait_ns = ctx->wait_ns;
+    p.extra_tx = ctx->extra_tx;
+    const int64_t grid = std::min<int64_t>(p.n_items, static_cast<int64_t>(ctx->sm_count) * occ);
+    void *args[] = {&p};
+    NB_CUDA(ctx, cudaLaunchKernel(e.fn, dim3(static_cast<unsigned>(grid)), dim3(e.warps * 32), args, e.smem, st));
+    ctx->last_launches = 1;
+    if (d.n_split > 1) {
+        nb::MergeParams mp{};
+        mp.d0 = d;
+        mp.n_clusters = 1;
+        mp.n_total = d.n_act;
+        nb::launch_merge(mp, st);
+        NB_CUDA(ctx, cudaGetLastError());
+        ctx->last_launches = 2;
+    }
+    return NB_OK;
+}
