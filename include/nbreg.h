@@ -79,7 +79,10 @@ typedef struct nb_kcfg {
     int32_t packed;     /* float forms: 0 = one FP32 operation per pair term; 1 = two
                          * i-particles per f32x2 instruction; 2 = two j-particles per
                          * f32x2 instruction (pair-interleaved j-set); 3 = as 2 with two
-                         * j-pairs per lane per step.  FP64 form: 0.                    */
+                         * j-pairs per lane per step; 4 = as 2 (two-float form only)
+                         * with the active set sorted along a Morton curve and compact
+                         * blocks computed in FP32 offsets from a shared frame centre.
+                         * FP64 form: 0.                                                 */
 } nb_kcfg;
 
 /* One independent cluster of a batched call (host struct; the pointers in it
@@ -257,6 +260,13 @@ int nb_sm_count(nb_ctx *ctx);
  * out after wait_ns, the kernels return early and nb_sync_status() reports
  * NB_ERR_TIMEOUT; the results of such calls are undefined. */
 int nb_debug_set_wait(nb_ctx *ctx, uint64_t wait_ns, uint32_t extra_tx);
+
+/* Diagnostic of the framed two-float kernel (tiling packed = 4, used by
+ * default for NB_MIXED calls with n_act >= 16384 and no velocity criterion):
+ * the number of blocks of the last framed call on the context and how many of
+ * them were compact enough for frame coordinates (the rest ran the per-pair
+ * two-float form).  Synchronises with the device. */
+int nb_debug_frame_stats(nb_ctx *ctx, int *compact_blocks, int *blocks);
 
 #ifdef __cplusplus
 }

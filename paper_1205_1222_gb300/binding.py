@@ -36,7 +36,7 @@ EXPORTS = [
     "nb_plan_launch", "nb_plan_destroy", "nb_plan_launches", "nb_step_host", "nb_sync_status",
     "nb_strerror", "nb_last_error", "nb_num_kernel_configs", "nb_get_kernel_config",
     "nb_set_kernel_config", "nb_get_active_config", "nb_time_regular_force", "nb_last_launches",
-    "nb_sm_count", "nb_debug_set_wait", "nb_regular_force_noalloc",
+    "nb_sm_count", "nb_debug_set_wait", "nb_regular_force_noalloc", "nb_debug_frame_stats",
 ]
 
 
@@ -105,6 +105,7 @@ def library():
         "nb_last_launches": ([P], cint),
         "nb_sm_count": ([P], cint),
         "nb_debug_set_wait": ([P, ctypes.c_uint64, ctypes.c_uint32], cint),
+        "nb_debug_frame_stats": ([P, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int)], cint),
         "nb_regular_force_noalloc": ([P, i64, i64, i32, P, P, P, i32, cint, P, P, P, P, P, P, P], cint),
     }
     for name, (args, res) in sig.items():
@@ -255,6 +256,13 @@ def nb_sm_count(ctx):
 
 def nb_debug_set_wait(ctx, wait_ns, extra_tx):
     _check(ctx, library().nb_debug_set_wait(ctx, int(wait_ns), int(extra_tx)), "nb_debug_set_wait")
+
+
+def nb_debug_frame_stats(ctx):
+    """(compact blocks, blocks) of the last framed call on the context."""
+    a, b = ctypes.c_int(), ctypes.c_int()
+    _check(ctx, library().nb_debug_frame_stats(ctx, ctypes.byref(a), ctypes.byref(b)), "nb_debug_frame_stats")
+    return a.value, b.value
 
 
 def nb_plan_create(ctx, clusters, mode, cfg=None):

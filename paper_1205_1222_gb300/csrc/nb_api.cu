@@ -15,6 +15,7 @@
 #include <cuda_runtime.h>
 
 #include "nb_aux.cuh"
+#include "nb_sort.cuh"
 #include "nbreg.h"
 
 using nb::ClusterDesc;
@@ -86,6 +87,10 @@ struct nb_ctx {
     uint32_t extra_tx = 0;
     void *stage = nullptr;   // nb_step_host device staging
     size_t stage_bytes = 0;
+    void *sort = nullptr;    // spatial sort and frames of the framed kernel
+    size_t sort_bytes = 0;
+    int *last_compact = nullptr;   // device count of compact blocks of the last framed call
+    int last_blocks = 0;
     std::string err;
 };
 
@@ -310,6 +315,62 @@ ClusterDesc make_desc(const Call &c)
     return d;
 }
 
+// Tiling used when the caller has not chosen one: the framed two-float
+// kernel for large active sets (its sort costs ~10 small launches), else the
+// first compiled tiling of the mode.
+constexpr int kFrameMinActive = 16384;
+
+nb_kcfg auto_cfg(int mode, int32_t n_act, const double *dtr)
+{
+    if (mode == NB_MIXED && n_act >= kFrameMinActive && !dtr) {
+        for (const auto &e : registry().all)
+            if (e.mode == mode && e.flags == 0 && e.packed == 4) return nb_kcfg{e.warps, e.ipw, e.jtile, 0, 4};
+    }
+    return default_cfg(mode);
+}
+
+// Order the active set along a Morton curve and build one frame per block of
+// `per_block` sorted particles (nb_sort.cu); fills d.perm and d.frames.
+int sort_and_frames(nb_ctx *ctx, const Call &c, int per_block, ClusterDesc &d, cudaStream_t st)
+{
+    const int n_blocks = (c.n_act + per_block - 1) / per_block;
+    const size_t need = nb::sort_scratch_bytes(c.n_act, n_blocks);
+    if (need > ctx->sort_bytes) {
+        cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+        if (cudaStreamIsCapturing(st, &cs) == cudaSuccess && cs != cudaStreamCaptureStatusNone) {
+            ctx->err = "sort scratch too small during stream capture";
+            return NB_ERR_STATE;
+        }
+        NB_CUDA(ctx, cudaStreamSynchronize(st));
+        if (ctx->sort) cudaFree(ctx->sort);
+        ctx->sort = nullptr;
+        ctx->sort_bytes = 0;
+        if (cudaMalloc(&ctx->sort, need) != cudaSuccess) {
+            cudaGetLastError();
+            ctx->err = "cannot allocate the sort scratch";
+            return NB_ERR_NOMEM;
+        }
+        ctx->sort_bytes = need;
+    }
+    nb::SortParams sp{};
+    sp.n_act = c.n_act;
+    sp.n_j = static_cast<int>(c.n_j);
+    sp.j_begin = c.j_begin;
+    sp.act = c.act;
+    sp.h = c.h;
+    sp.pos_hi = ctx->mx_hi;
+    sp.pos_lo = ctx->mx_lo;
+    sp.vel_hi = ctx->mv_hi;
+    sp.vel_lo = ctx->mv_lo;
+    const nb::SortBuffers sb = nb::carve_sort(ctx->sort, c.n_act, n_blocks);
+    d.perm = nb::launch_sort_and_frames(sp, sb, per_block, n_blocks, st);
+    d.frames = sb.frames;
+    NB_CUDA(ctx, cudaGetLastError());
+    ctx->last_compact = sb.n_compact;
+    ctx->last_blocks = n_blocks;
+    return NB_OK;
+}
+
 int run_single(nb_ctx *ctx, const Call &c, const nb_kcfg *cfg_override, cudaStream_t st)
 {
     int rc = check_call(ctx, c);
@@ -317,7 +378,8 @@ int run_single(nb_ctx *ctx, const Call &c, const nb_kcfg *cfg_override, cudaStre
     ctx->last_launches = 0;
     if (c.n_act == 0) return NB_OK;
     DeviceGuard guard(ctx->device);
-    const nb_kcfg cfg = cfg_override ? *cfg_override : (ctx->cfg_set[c.mode] ? ctx->cfg[c.mode] : default_cfg(c.mode));
+    const nb_kcfg cfg = cfg_override ? *cfg_override
+                                     : (ctx->cfg_set[c.mode] ? ctx->cfg[c.mode] : auto_cfg(c.mode, c.n_act, c.dtr));
     const int flags = (c.dtr ? 1 : 0) | (c.pot ? 2 : 0);
     int idx = find_entry(c.mode, cfg, flags);
     if (idx < 0) { ctx->err = "no kernel for this mode"; return NB_ERR_UNSUPPORTED; }
@@ -332,6 +394,12 @@ int run_single(nb_ctx *ctx, const Call &c, const nb_kcfg *cfg_override, cudaStre
     rc = grow_scratch(ctx, cluster_scratch(d), st);
     if (rc != NB_OK) return rc;
     carve_scratch(d, static_cast<char *>(ctx->scratch));
+    int sort_launches = 0;
+    if (e.packed == 4) {   // framed kernel: spatial order of the active set and per-block frames
+        rc = sort_and_frames(ctx, c, e.warps * e.ipw, d, st);
+        if (rc != NB_OK) return rc;
+        sort_launches = 10;
+    }
 
     nb::RegfParams p{};
     p.js = tile_streams(ctx, c.mode, e);
@@ -348,7 +416,7 @@ int run_single(nb_ctx *ctx, const Call &c, const nb_kcfg *cfg_override, cudaStre
     void *args[] = {&p};
     NB_CUDA(ctx, cudaLaunchKernel(e.fn, dim3(static_cast<unsigned>(grid)), dim3(e.warps * 32), args,
                                   e.smem, st));
-    ctx->last_launches = 1;
+    ctx->last_launches = 1 + sort_launches;
     if (d.n_split > 1) {
         nb::MergeParams mp{};
         mp.d0 = d;
@@ -356,7 +424,7 @@ int run_single(nb_ctx *ctx, const Call &c, const nb_kcfg *cfg_override, cudaStre
         mp.n_total = d.n_act;
         nb::launch_merge(mp, st);
         NB_CUDA(ctx, cudaGetLastError());
-        ctx->last_launches = 2;
+        ctx->last_launches = 2 + sort_launches;
     }
     return NB_OK;
 }
@@ -432,7 +500,7 @@ void nb_destroy(nb_ctx *c)
     DeviceGuard guard(c->device);
     cudaDeviceSynchronize();
     void *bufs[] = {c->pos64, c->vel64, c->mx_hi, c->mx_lo, c->mv_hi, c->mv_lo, c->pos32, c->vel32,
-                    c->d_status, c->scratch, c->stage};
+                    c->d_status, c->scratch, c->stage, c->sort};
     for (void *b : bufs)
         if (b) cudaFree(b);
     for (float4 *b : c->pim)
@@ -899,6 +967,18 @@ int nb_plan_launch(nb_plan *p, nb_stream_t stream)
     if (!p->exec) { p->ctx->err = "plan has no captured graph"; return NB_ERR_STATE; }
     DeviceGuard guard(p->ctx->device);
     NB_CUDA(p->ctx, cudaGraphLaunch(p->exec, static_cast<cudaStream_t>(stream)));
+    return NB_OK;
+}
+
+int nb_debug_frame_stats(nb_ctx *ctx, int *compact_blocks, int *blocks)
+{
+    if (!ctx || !compact_blocks || !blocks) return NB_ERR_ARG;
+    *blocks = ctx->last_blocks;
+    *compact_blocks = 0;
+    if (ctx->last_compact) {
+        DeviceGuard guard(ctx->device);
+        NB_CUDA(ctx, cudaMemcpy(compact_blocks, ctx->last_compact, sizeof(int), cudaMemcpyDeviceToHost));
+    }
     return NB_OK;
 }
 

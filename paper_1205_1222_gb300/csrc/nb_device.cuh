@@ -8,6 +8,8 @@
 
 namespace nb {
 
+struct FrameRec;   // nb_sort.cuh
+
 // Device status bits (OR-ed into the context's status word).
 enum : int {
     DEV_TIMEOUT = 1,    // a bounded wait on a copy ran out
@@ -43,6 +45,10 @@ struct ClusterDesc {
     double *pF;
     int32_t *pcnt;
     int32_t *plist;
+    // framed kernels: processing order of the active set (slot -> position in
+    // act) and one frame per block of W*I consecutive slots; both nullptr otherwise
+    const int32_t *perm;
+    const FrameRec *frames;
 };
 
 struct RegfParams {

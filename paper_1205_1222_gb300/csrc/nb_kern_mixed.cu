@@ -11,10 +11,11 @@ static const KernelEntry g_mixed[] = {
     NB_KERNEL_ENTRY3(PairMixed, 1, 16, 2, 512, 4, 1, 1, 1),
     NB_KERNEL_ENTRY3(PairMixed, 1, 16, 2, 512, 4, 1, 2, 1),
     NB_KERNEL_ENTRY3(PairMixed, 1, 16, 2, 512, 4, 1, 3, 1),
-    NB_KERNEL_ENTRY3(PairMixed, 1, 16, 2, 512, 6, 2, 0, 1),
-    NB_KERNEL_ENTRY3(PairMixed, 1, 12, 2, 512, 6, 2, 0, 1),
-    NB_KERNEL_ENTRY3(PairMixed, 1, 8, 2, 256, 6, 1, 0, 2),
-    NB_KERNEL_ENTRY3(PairMixed, 1, 12, 2, 512, 6, 1, 0, 1),
+    NB_KERNEL_ENTRY3(PairMixed, 1, 16, 2, 512, 4, 2, 0, 1),
+    NB_KERNEL_ENTRY3(PairMixed, 1, 12, 2, 512, 4, 1, 0, 1),
+    NB_KERNEL_ENTRY4(16, 2, 512, 4, 1, 0, 1),
+    NB_KERNEL_ENTRY4(16, 2, 512, 4, 1, 2, 1),
+    NB_KERNEL_ENTRY4(12, 2, 512, 4, 1, 0, 1),
     NB_KERNEL_ENTRY(FormMixed, 1, 8, 4, 512, 0),
     NB_KERNEL_ENTRY(FormMixed, 1, 4, 4, 512, 0),
     NB_KERNEL_ENTRY(FormMixed, 1, 8, 2, 512, 0),

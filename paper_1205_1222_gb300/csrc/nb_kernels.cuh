@@ -15,6 +15,16 @@
 #define NB_KERNEL_ENTRY3(FORM, MODE, W, I, JT, NST, U, FL, MINB)                        \
     {                                                                                   \
         MODE, W, I, JT, FL, (U) == 1 ? 2 : 3,                                           \
-            reinterpret_cast<const void *>(&nb::regf3_kernel<FORM, W, I, JT, NST, U, FL, MINB>), \
+            reinterpret_cast<const void *>(&nb::regf3_kernel<FORM, nb::NoFrame, W, I, JT, NST, U, FL, MINB>), \
             nb::pair_smem_bytes<FORM, W, I, JT, NST>(((FL) & 2) != 0)                  \
+    }
+
+// Framed two-float kernel (packed = 4): compact blocks of the spatially sorted
+// active set use frame coordinates, the others the per-pair two-float form.
+#define NB_KERNEL_ENTRY4(W, I, JT, NST, U, FL, MINB)                                    \
+    {                                                                                   \
+        1, W, I, JT, FL, 4,                                                             \
+            reinterpret_cast<const void *>(                                             \
+                &nb::regf3_kernel<nb::PairMixed, nb::FramedMixed, W, I, JT, NST, U, FL, MINB>), \
+            nb::pair_smem_bytes<nb::PairMixed, W, I, JT, NST>(((FL) & 2) != 0)         \
     }

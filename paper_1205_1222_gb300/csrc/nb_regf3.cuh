@@ -27,8 +27,15 @@
 #include <type_traits>
 
 #include "nb_pair_ops.cuh"
+#include "nb_sort.cuh"
 
 namespace nb {
+
+// Frame centre of a block of active particles, position and velocity in
+// two-float (hi + lo) form (used by the framed form only).
+struct Frame2 {
+    float xh[3], xl[3], vh[3], vl[3];
+};
 
 // Two-float (mixed) form, pair-interleaved: 7 float4 streams per j-pair
 //   q0 (xh_a, xh_b, yh_a, yh_b)  q1 (zh_a, zh_b, m_a, m_b)  q2 (xl_a, xl_b, yl_a, yl_b)
@@ -69,7 +76,8 @@ struct PairMixed {
         }
         fix(s.m, 0.f);
     }
-    static __device__ __forceinline__ void set_i(IB &ib, const JSet &soa, int64_t slot, float h2, float dtr)
+    static __device__ __forceinline__ void set_i(IB &ib, const JSet &soa, int64_t slot, float h2, float dtr,
+                                                 const Frame2 &)
     {
         FormMixed::IS a;
         FormMixed::clear_i(a);
@@ -140,7 +148,8 @@ struct PairFP32 {
         }
         fix(s.m, 0.f);
     }
-    static __device__ __forceinline__ void set_i(IB &ib, const JSet &soa, int64_t slot, float h2, float dtr)
+    static __device__ __forceinline__ void set_i(IB &ib, const JSet &soa, int64_t slot, float h2, float dtr,
+                                                 const Frame2 &)
     {
         FormFP32::IS a;
         FormFP32::clear_i(a);
@@ -167,14 +176,76 @@ struct PairFP32 {
     }
 };
 
+// Framed two-float form.  A tile of the pair-interleaved two-float stream is
+// rewritten in place (frame_tile) as FP32 offsets from the block's frame
+// centre c, in the FP32 stream layout; the i-values are c - x_i, formed in
+// two-float and rounded once.  A pair term is then the FP32 form's
+// arithmetic: dx = (x_j - c) + (c - x_i), one add per component.
+struct FramedMixed : PairFP32 {
+    static __device__ __forceinline__ void set_i(IB &ib, const JSet &soa, int64_t slot, float h2, float dtr,
+                                                 const Frame2 &fr)
+    {
+        FormMixed::IS a;
+        FormMixed::clear_i(a);
+        if (slot >= 0) FormMixed::load_i(a, soa, slot);
+        for (int c = 0; c < 3; c++) {
+            ib.nx[c] = bc((fr.xh[c] - a.xh[c]) + (fr.xl[c] - a.xl[c]));
+            ib.nv[c] = bc((fr.vh[c] - a.vh[c]) + (fr.vl[c] - a.vl[c]));
+        }
+        ib.h2 = bc(h2);
+        ib.dtr = bc(dtr);
+    }
+};
+
+// Rewrite the j-pairs of a two-float tile (7 streams of NP float4) in place as
+// FP32 offsets from the frame centre, in the FP32 layout (streams 0..3).  Each
+// lane reads all seven float4 of its pairs before writing any of them.
+template <int NP>
+__device__ __forceinline__ void frame_tile(unsigned char *st, const Frame2 &fr, int lane)
+{
+    ulonglong2 *q = reinterpret_cast<ulonglong2 *>(st);
+    f2 nxh[3], nxl[3], nvh[3], nvl[3];
+    for (int c = 0; c < 3; c++) {
+        nxh[c] = bc(-fr.xh[c]);
+        nxl[c] = bc(-fr.xl[c]);
+        nvh[c] = bc(-fr.vh[c]);
+        nvl[c] = bc(-fr.vl[c]);
+    }
+    for (int pl = lane; pl < NP; pl += 32) {
+        const ulonglong2 a = q[pl], b = q[NP + pl], c = q[2 * NP + pl], d = q[3 * NP + pl];
+        const ulonglong2 e = q[4 * NP + pl], f = q[5 * NP + pl], g = q[6 * NP + pl];
+        ulonglong2 o0, o1, o2, o3;
+        o0.x = add2(add2(a.x, nxh[0]), add2(c.x, nxl[0]));
+        o0.y = add2(add2(a.y, nxh[1]), add2(c.y, nxl[1]));
+        o1.x = add2(add2(b.x, nxh[2]), add2(d.x, nxl[2]));
+        o1.y = b.y;   // masses
+        o2.x = add2(add2(d.y, nvh[0]), add2(f.x, nvl[0]));
+        o2.y = add2(add2(e.x, nvh[1]), add2(f.y, nvl[1]));
+        o3.x = add2(add2(e.y, nvh[2]), add2(g.x, nvl[2]));
+        o3.y = 0ull;
+        q[pl] = o0;
+        q[NP + pl] = o1;
+        q[2 * NP + pl] = o2;
+        q[3 * NP + pl] = o3;
+    }
+}
+
+// Marker for the kernels without frames.
+struct NoFrame {};
+
+template <class T>
+struct FormTag {
+    using type = T;
+};
+
 template <class Fm, int W, int I, int JT, int NST_>
 struct PairLayout {
     static constexpr int NST = NST_;                               // stages of the j-tile ring
     static constexpr int NP = JT / 2;                              // j-pairs per tile
     static constexpr int STAGE = Fm::NS * 16 * NP;
-    static constexpr int STAGES = 128;                             // barriers + release counters first
-    static constexpr int TOT = STAGES + NST * STAGE;
+    static constexpr int STAGES = 256;                             // barriers and counters first
     // float-float totals: one (hi, lo) float2 per (warp, i, component, lane)
+    static constexpr int TOT = STAGES + NST * STAGE;
     __host__ __device__ static constexpr int tot_bytes(bool pot) { return W * I * (pot ? 7 : 6) * 32 * 8; }
     __host__ __device__ static constexpr int cnt(bool pot) { return TOT + tot_bytes(pot); }
     __host__ __device__ static constexpr int gi(bool pot) { return cnt(pot) + W * I * 4; }
@@ -212,12 +283,25 @@ __device__ __forceinline__ void issue_pairs(const RegfParams &p, const TileCurso
         tma_bulk_g2s(st + k * NP * 16, static_cast<const unsigned char *>(p.js.s[k]) + first * 16, bytes, b);
 }
 
-template <class Fm, int W, int I, int JT, int NSTAGE, int U, int FLAGS, int MINB>
+__device__ __forceinline__ void mbar_arrive(uint64_t *bar)
+{
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
+}
+
+__device__ __forceinline__ void fence_proxy_async_smem()
+{
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+
+// Fm: the exact (per-pair two-float or FP32) form; Ff: NoFrame, or the framed
+// form used for the work items whose block of active particles is compact.
+template <class Fm, class Ff, int W, int I, int JT, int NSTAGE, int U, int FLAGS, int MINB>
 __global__ void __launch_bounds__(W * 32, MINB) regf3_kernel(const RegfParams p)
 {
-    static_assert(NSTAGE <= 12, "ring barriers and release counters share the first 128 bytes");
+    static_assert(NSTAGE <= 10, "ring barriers and counters share the first 256 bytes");
     static_assert((JT / 64) % U == 0, "a tile holds a whole number of steps");
     using L = PairLayout<Fm, W, I, JT, NSTAGE>;
+    constexpr bool FRAMED = !std::is_same<Ff, NoFrame>::value;
     constexpr bool VC = (FLAGS & 1) != 0;
     constexpr bool POT = (FLAGS & 2) != 0;
     constexpr int NC = POT ? 7 : 6;
@@ -226,12 +310,12 @@ __global__ void __launch_bounds__(W * 32, MINB) regf3_kernel(const RegfParams p)
     constexpr int STEPS = NP / 32;                                // a step covers 64 j
     constexpr int FOLD_STEPS = 64;                                // steps (128 j per lane) per FP32 partial
     constexpr int FOLD_TILES = STEPS >= FOLD_STEPS ? 1 : FOLD_STEPS / STEPS;
-    using JP = typename Fm::JP;
-    using IB = typename Fm::IB;
 
     extern __shared__ __align__(128) unsigned char smem[];
-    uint64_t *full = reinterpret_cast<uint64_t *>(smem);
-    int *rel = reinterpret_cast<int *>(smem + 8 * NST);
+    uint64_t *full = reinterpret_cast<uint64_t *>(smem);          // tile landed (TMA)
+    uint64_t *xf = full + NST;                                    // tile rewritten in frame coordinates
+    int *rel = reinterpret_cast<int *>(xf + NST);                 // warps done with the stage
+    int *claim = rel + NST;                                       // warps that reached the stage
     unsigned char *stages = smem + L::STAGES;
     float2 *s_tot = reinterpret_cast<float2 *>(smem + L::TOT);
     int *s_cnt = reinterpret_cast<int *>(smem + L::cnt(POT));
@@ -245,7 +329,9 @@ __global__ void __launch_bounds__(W * 32, MINB) regf3_kernel(const RegfParams p)
     if (tid == 0) {
         for (int s = 0; s < NST; s++) {
             mbar_init(&full[s], 1);
+            mbar_init(&xf[s], 1);
             rel[s] = 0;
+            claim[s] = 0;
         }
         fence_mbar_init();
         TileCursor c0 = la;
@@ -264,25 +350,26 @@ __global__ void __launch_bounds__(W * 32, MINB) regf3_kernel(const RegfParams p)
     int *mygi = s_gi + warp * I;
     ClusterDesc &d = s_d[warp];
 
-    for (int64_t item = blockIdx.x; item < p.n_items && !aborted; item += gridDim.x) {
-        if (lane == 0) d = p.table ? p.table[find_cluster(p, item)] : p.d0;
-        __syncwarp();
-        const int64_t local = item - d.item_begin;
-        const int ib = static_cast<int>(local / d.n_split);
-        const int sp = static_cast<int>(local - static_cast<int64_t>(ib) * d.n_split);
+    // One work item (i-block ib, j-split sp) with the pair arithmetic of form P.
+    auto run_item = [&](auto form_tag, int ib, int sp, bool framed_item, const Frame2 &fr) {
+        using P = typename decltype(form_tag)::type;
+        using JP = typename P::JP;
+        using IB = typename P::IB;
         const int tb = sp * d.tiles_per_split;
         const int te = min(tb + d.tiles_per_split, d.n_tiles);
-
         IB ipart[I];
         Acc2 acc[I];
+        int oidx[I];                 // output row of each i (its position in act)
         const int i0 = (ib * W + warp) * I;
 #pragma unroll
         for (int k = 0; k < I; k++) {
-            const int idx = i0 + k;
+            const int slot_i = i0 + k;
+            int idx = -1;
             int64_t slot = -1;
             float h2v = -1.f, dtv = 0.f;
             int gi = -1;
-            if (idx < d.n_act) {
+            if (slot_i < d.n_act) {
+                idx = d.perm ? d.perm[slot_i] : slot_i;
                 const int a = d.act[idx];
                 const double hv = d.h[idx];
                 if (a >= 0 && a < d.n_j && hv >= 0.0 && hv <= DBL_MAX) {
@@ -294,8 +381,9 @@ __global__ void __launch_bounds__(W * 32, MINB) regf3_kernel(const RegfParams p)
                     atomicOr(p.status, DEV_BAD_INPUT);
                 }
             }
+            oidx[k] = gi >= 0 ? idx : -1;
             if (lane == 0) { mygi[k] = gi; mycnt[k] = 0; }
-            Fm::set_i(ipart[k], p.soa, slot, h2v, dtv);
+            P::set_i(ipart[k], p.soa, slot, h2v, dtv, fr);
             for (int c = 0; c < 3; c++) acc[k].f[c] = acc[k].j[c] = 0ull;
             acc[k].p = 0ull;
             for (int c = 0; c < NC; c++) mytot[(k * NC + c) * 32] = make_float2(0.f, 0.f);
@@ -305,7 +393,21 @@ __global__ void __launch_bounds__(W * 32, MINB) regf3_kernel(const RegfParams p)
         for (int t = tb; t < te; ++t, ++g) {
             const int s = g % NST;
             if (!mbar_wait_bounded(&full[s], (g / NST) & 1, p.wait_ns)) { aborted = true; break; }
-            const unsigned char *st = stages + s * L::STAGE;
+            unsigned char *st = stages + s * L::STAGE;
+            if constexpr (FRAMED) {
+                // the first warp to reach the tile rewrites it in frame coordinates
+                int first = 0;
+                if (lane == 0) first = atomicAdd(&claim[s], 1) == 0;
+                first = __shfl_sync(0xffffffffu, first, 0);
+                if (first) {
+                    if (framed_item) frame_tile<NP>(st, fr, lane);
+                    __syncwarp();
+                    if (lane == 0) mbar_arrive(&xf[s]);
+                } else if (!mbar_wait_bounded(&xf[s], (g / NST) & 1, p.wait_ns)) {
+                    aborted = true;
+                    break;
+                }
+            }
             const int jt0 = t * JT;
             const int count = min(JT, d.n_j - jt0);
 
@@ -321,11 +423,11 @@ __global__ void __launch_bounds__(W * 32, MINB) regf3_kernel(const RegfParams p)
                 for (int u = 0; u < U; u++) {
                     const int pl = (k * U + u) * 32 + lane;
                     JP jp;
-                    Fm::template load_j<NP>(jp, st, pl);
-                    if (tail) Fm::mask(jp, 2 * pl < count, 2 * pl + 1 < count);
+                    P::template load_j<NP>(jp, st, pl);
+                    if (tail) P::mask(jp, 2 * pl < count, 2 * pl + 1 < count);
 #pragma unroll
                     for (int q = 0; q < I; q++)
-                        if (Fm::template pair<VC, POT>(ipart[q], jp, acc[q])) bits[q] |= 1u << (k * U + u);
+                        if (P::template pair<VC, POT>(ipart[q], jp, acc[q])) bits[q] |= 1u << (k * U + u);
                 }
             };
             if (count == JT) {
@@ -345,10 +447,10 @@ __global__ void __launch_bounds__(W * 32, MINB) regf3_kernel(const RegfParams p)
                     todo &= todo - 1;
                     const int pl = unit * 32 + lane;
                     JP jp;
-                    Fm::template load_j<NP>(jp, st, pl);
-                    if (count < JT) Fm::mask(jp, 2 * pl < count, 2 * pl + 1 < count);
+                    P::template load_j<NP>(jp, st, pl);
+                    if (count < JT) P::mask(jp, 2 * pl < count, 2 * pl + 1 < count);
                     bool fa, fb;
-                    Fm::template test<VC>(ipart[q], jp, fa, fb);
+                    P::template test<VC>(ipart[q], jp, fa, fb);
                     const int ja = jt0 + 2 * pl;
                     const int gq = mygi[q];
                     const bool xa = fa && ja != gq, xb = fb && ja + 1 != gq;
@@ -359,7 +461,7 @@ __global__ void __launch_bounds__(W * 32, MINB) regf3_kernel(const RegfParams p)
                     const int pa = c0 + __popc(ma & lt) + __popc(mb & lt);
                     const int pb = pa + (xa ? 1 : 0);
                     if ((xa && pa < d.cap) || (xb && pb < d.cap)) {
-                        const int64_t idx = i0 + q;
+                        const int64_t idx = oidx[q];
                         int32_t *row = d.n_split == 1
                                            ? d.list + idx * d.cap
                                            : d.plist + (static_cast<int64_t>(sp) * d.n_act + idx) * d.cap;
@@ -378,6 +480,10 @@ __global__ void __launch_bounds__(W * 32, MINB) regf3_kernel(const RegfParams p)
                 __threadfence_block();
                 if (atomicAdd(&rel[s], 1) == W - 1) {
                     rel[s] = 0;
+                    if constexpr (FRAMED) {
+                        claim[s] = 0;
+                        fence_proxy_async_smem();   // the stage was written through the generic proxy
+                    }
                     if (la.item < p.n_items) issue_pairs<Fm, JT, NST>(p, la, g + NST, full, stages);
                 }
             }
@@ -399,9 +505,9 @@ __global__ void __launch_bounds__(W * 32, MINB) regf3_kernel(const RegfParams p)
                 }
             }
         }
-        if (aborted) break;
+        if (aborted) return;
 
-        // reduce the float-float totals over both halves and the 32 lanes, then write
+        // reduce the float-float totals over the 32 lanes, then write
 #pragma unroll
         for (int q = 0; q < I; q++) {
             double out[7] = {0, 0, 0, 0, 0, 0, 0};
@@ -415,8 +521,8 @@ __global__ void __launch_bounds__(W * 32, MINB) regf3_kernel(const RegfParams p)
                 }
                 out[c] = static_cast<double>(hi) + static_cast<double>(lo);
             }
-            const int64_t i = i0 + q;
-            if (lane == 0 && mygi[q] >= 0) {
+            const int64_t i = oidx[q];
+            if (lane == 0 && i >= 0) {
                 const int cnt = mycnt[q];
                 if (d.n_split == 1) {
                     for (int c = 0; c < 3; c++) { d.F[3 * i + c] = out[c]; d.J[3 * i + c] = out[3 + c]; }
@@ -431,6 +537,32 @@ __global__ void __launch_bounds__(W * 32, MINB) regf3_kernel(const RegfParams p)
             }
         }
         __syncwarp();
+    };
+
+    for (int64_t item = blockIdx.x; item < p.n_items && !aborted; item += gridDim.x) {
+        if (lane == 0) d = p.table ? p.table[find_cluster(p, item)] : p.d0;
+        __syncwarp();
+        const int64_t local = item - d.item_begin;
+        const int ib = static_cast<int>(local / d.n_split);
+        const int sp = static_cast<int>(local - static_cast<int64_t>(ib) * d.n_split);
+        Frame2 fr{};
+        bool framed_item = false;
+        if constexpr (FRAMED) {
+            if (d.frames) {
+                const FrameRec f = d.frames[ib];
+                framed_item = f.compact != 0;
+                for (int c = 0; c < 3; c++) {
+                    fr.xh[c] = __double2float_rn(f.cx[c]);
+                    fr.xl[c] = __double2float_rn(f.cx[c] - static_cast<double>(fr.xh[c]));
+                    fr.vh[c] = __double2float_rn(f.cv[c]);
+                    fr.vl[c] = __double2float_rn(f.cv[c] - static_cast<double>(fr.vh[c]));
+                }
+            }
+            if (framed_item) run_item(FormTag<Ff>{}, ib, sp, true, fr);
+            else run_item(FormTag<Fm>{}, ib, sp, false, fr);
+        } else {
+            run_item(FormTag<Fm>{}, ib, sp, false, fr);
+        }
     }
 
     if (aborted && lane == 0) {

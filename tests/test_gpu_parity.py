@@ -378,3 +378,37 @@ def test_config5_offset_hard_pairs(cfg5):
     g = gpu_run(w, "fp32")
     print("fp32 list mismatches at offset 1e3:", list_mismatches(g, o, w.cap),
           "max force err", rel_err(g["F"], o["F"]).max())
+
+
+# ---------------------------------------------------------- framed kernel
+
+@pytest.mark.parametrize("offset,pairs", [(0.0, 0.0), (1e3, 0.1)])
+def test_framed_two_float_kernel(offset, pairs):
+    """Morton-sorted active set with frame coordinates for compact blocks: exact
+    lists and the two-float tolerances, also with a 1e3 centre offset and hard
+    pairs; most blocks of an all-active set are compact."""
+    w = inputs.cluster(20000, 31, 64, 256, offset=offset, pair_frac=pairs)
+    framed = None
+    for i in range(B.nb_num_kernel_configs(B.NB_MIXED)):
+        c = B.nb_get_kernel_config(B.NB_MIXED, i)
+        if c.packed == 4:
+            framed = c
+            break
+    assert framed is not None
+    with Context(w.n) as ctx:
+        g = gpu_run(w, "mixed", ctx=ctx, cfg=framed)
+        compact, blocks = B.nb_debug_frame_stats(ctx.h)
+    assert g["status"] == 0
+    assert blocks == (w.n_act + framed.warps * framed.ipw - 1) // (framed.warps * framed.ipw)
+    print("compact blocks", compact, "of", blocks)
+    assert compact > 0.5 * blocks, (compact, blocks)
+    compare(g, oracle_run(w), w.cap, "mixed")
+
+
+def test_framed_kernel_is_the_default_for_large_active_sets(cfg2):
+    with Context(cfg2.n) as ctx:
+        g = gpu_run(cfg2, "mixed", ctx=ctx)
+        compact, blocks = B.nb_debug_frame_stats(ctx.h)
+    assert blocks > 0 and compact > 0
+    assert g["launches"] > 2          # the sort kernels ran
+    compare(g, oracle_run(cfg2), cfg2.cap, "mixed")
