@@ -428,19 +428,21 @@ def run_ours(args):
     forms = {}
     outs = {args.mode: g_main}
     if not args.no_forms:
-        for mode in ("fp64", "fp32", "mixed"):
-            if mode == args.mode:
-                forms[mode] = {"value": value / world, "ms_per_step": ms, "kernel_ms": fms}
+        # the exact two-float pair form (two-float velocity differences too) beside the default
+        for label, mode, cfg in (("fp64", "fp64", ""), ("fp32", "fp32", ""), ("mixed", "mixed", ""),
+                                 ("mixed_exact_pair", "mixed", "16,2,512,2")):
+            if mode == args.mode and not cfg and not args.config:
+                forms[label] = {"value": value / world, "ms_per_step": ms, "kernel_ms": fms}
                 continue
-            rr = Runner(w, mode, device)
+            rr = Runner(w, mode, device, cfg)
             rr.predict(); rr.force()
             torch.cuda.synchronize(device)
             k = 2 if mode == "fp64" else args.steps
             sm_, fm_ = rr.timed(k, flush)
-            forms[mode] = {"value": inter / (statistics.mean(sm_) / 1e3), "ms_per_step": statistics.mean(sm_),
-                           "kernel_ms": statistics.mean(fm_), "steps": k,
-                           "frac_fp32_peak": FLOPS_PER_INTERACTION * inter / (statistics.mean(fm_) / 1e3) / 1e12 / peak}
-            outs[mode] = rr.outputs()
+            forms[label] = {"value": inter / (statistics.mean(sm_) / 1e3), "ms_per_step": statistics.mean(sm_),
+                            "kernel_ms": statistics.mean(fm_), "steps": k, "tiling": rr.cfg,
+                            "frac_fp32_peak": FLOPS_PER_INTERACTION * inter / (statistics.mean(fm_) / 1e3) / 1e12 / peak}
+            outs[label] = rr.outputs()
             rr.close()
         line["forms"] = forms
     if not args.no_e2e:

@@ -81,8 +81,9 @@ typedef struct nb_kcfg {
                          * f32x2 instruction (pair-interleaved j-set); 3 = as 2 with two
                          * j-pairs per lane per step; 4 = as 2 (two-float form only)
                          * with the active set sorted along a Morton curve and compact
-                         * blocks computed in FP32 offsets from a shared frame centre.
-                         * FP64 form: 0.                                                 */
+                         * blocks computed in FP32 offsets from a shared frame centre;
+                         * 5 = as 2 (two-float form only) with two-float positions and
+                         * FP32 velocity differences.  FP64 form: 0.                     */
 } nb_kcfg;
 
 /* One independent cluster of a batched call (host struct; the pointers in it
@@ -261,9 +262,8 @@ int nb_sm_count(nb_ctx *ctx);
  * NB_ERR_TIMEOUT; the results of such calls are undefined. */
 int nb_debug_set_wait(nb_ctx *ctx, uint64_t wait_ns, uint32_t extra_tx);
 
-/* Diagnostic of the framed two-float kernel (tiling packed = 4, used by
- * default for NB_MIXED calls with n_act >= 16384 and no velocity criterion):
- * the number of blocks of the last framed call on the context and how many of
+/* Diagnostic of the framed two-float kernel (tiling packed = 4, chosen with
+ * nb_set_kernel_config): the number of blocks of the last framed call on the context and how many of
  * them were compact enough for frame coordinates (the rest ran the per-pair
  * two-float form).  Synchronises with the device. */
 int nb_debug_frame_stats(nb_ctx *ctx, int *compact_blocks, int *blocks);

@@ -315,20 +315,6 @@ ClusterDesc make_desc(const Call &c)
     return d;
 }
 
-// Tiling used when the caller has not chosen one: the framed two-float
-// kernel for large active sets (its sort costs ~10 small launches), else the
-// first compiled tiling of the mode.
-constexpr int kFrameMinActive = 16384;
-
-nb_kcfg auto_cfg(int mode, int32_t n_act, const double *dtr)
-{
-    if (mode == NB_MIXED && n_act >= kFrameMinActive && !dtr) {
-        for (const auto &e : registry().all)
-            if (e.mode == mode && e.flags == 0 && e.packed == 4) return nb_kcfg{e.warps, e.ipw, e.jtile, 0, 4};
-    }
-    return default_cfg(mode);
-}
-
 // Order the active set along a Morton curve and build one frame per block of
 // `per_block` sorted particles (nb_sort.cu); fills d.perm and d.frames.
 int sort_and_frames(nb_ctx *ctx, const Call &c, int per_block, ClusterDesc &d, cudaStream_t st)
@@ -379,7 +365,7 @@ int run_single(nb_ctx *ctx, const Call &c, const nb_kcfg *cfg_override, cudaStre
     if (c.n_act == 0) return NB_OK;
     DeviceGuard guard(ctx->device);
     const nb_kcfg cfg = cfg_override ? *cfg_override
-                                     : (ctx->cfg_set[c.mode] ? ctx->cfg[c.mode] : auto_cfg(c.mode, c.n_act, c.dtr));
+                                     : (ctx->cfg_set[c.mode] ? ctx->cfg[c.mode] : default_cfg(c.mode));
     const int flags = (c.dtr ? 1 : 0) | (c.pot ? 2 : 0);
     int idx = find_entry(c.mode, cfg, flags);
     if (idx < 0) { ctx->err = "no kernel for this mode"; return NB_ERR_UNSUPPORTED; }

@@ -1,5 +1,7 @@
 // Compiled configurations of the two-float (NB_MIXED) regular-force kernel:
-// packed f32x2 j-pair kernels and the scalar kernel.  The first entry of each
+// packed f32x2 j-pair kernels (two-float positions with FP32 velocity
+// differences, the default; the exact two-float pair form; the framed form)
+// and the scalar kernel.  The first entry of each
 // flag value is the default; all flag-0 entries form the autotuner's search
 // space.
 #include "nb_kernels.cuh"
@@ -7,6 +9,11 @@
 namespace nb {
 
 static const KernelEntry g_mixed[] = {
+    NB_KERNEL_ENTRY5(16, 2, 512, 4, 0, 1),
+    NB_KERNEL_ENTRY5(16, 2, 512, 4, 1, 1),
+    NB_KERNEL_ENTRY5(16, 2, 512, 4, 2, 1),
+    NB_KERNEL_ENTRY5(16, 2, 512, 4, 3, 1),
+    NB_KERNEL_ENTRY5(12, 2, 512, 4, 0, 1),
     NB_KERNEL_ENTRY3(PairMixed, 1, 16, 2, 512, 4, 1, 0, 1),
     NB_KERNEL_ENTRY3(PairMixed, 1, 16, 2, 512, 4, 1, 1, 1),
     NB_KERNEL_ENTRY3(PairMixed, 1, 16, 2, 512, 4, 1, 2, 1),

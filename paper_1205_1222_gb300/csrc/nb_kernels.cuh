@@ -19,6 +19,14 @@
             nb::pair_smem_bytes<FORM, W, I, JT, NST>(((FL) & 2) != 0)                  \
     }
 
+// Two-float positions with FP32 velocities (packed = 5), j-pair kernel.
+#define NB_KERNEL_ENTRY5(W, I, JT, NST, FL, MINB)                                       \
+    {                                                                                   \
+        1, W, I, JT, FL, 5,                                                             \
+            reinterpret_cast<const void *>(&nb::regf3_kernel<nb::PairMixedX, nb::NoFrame, W, I, JT, NST, 1, FL, MINB>), \
+            nb::pair_smem_bytes<nb::PairMixedX, W, I, JT, NST>(((FL) & 2) != 0)        \
+    }
+
 // Framed two-float kernel (packed = 4): compact blocks of the spatially sorted
 // active set use frame coordinates, the others the per-pair two-float form.
 #define NB_KERNEL_ENTRY4(W, I, JT, NST, U, FL, MINB)                                    \

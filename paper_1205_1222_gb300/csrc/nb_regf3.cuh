@@ -117,6 +117,86 @@ struct PairMixed {
     }
 };
 
+// Two-float positions, FP32 velocities: the first five streams of the
+// two-float layout (q0..q4: xh, m, xl, vh).  x_j - x_i keeps the two-float
+// difference of PairMixed; v_j - v_i is the FP32 difference of the rounded
+// velocities, whose absolute error u (|v_i| + |v_j|) stays at the level of
+// the other FP32 roundings of a pair term when the velocities are given in
+// a frame where they are of the order of the velocity dispersion (the
+// centre-of-mass frame of an N-body integration).  Positions get no such
+// help: a cluster far from the origin, or a close pair, needs the low parts.
+struct PairMixedX {
+    static constexpr int NS = 5;
+    struct IB {
+        f2 nxh[3], nxl[3], nv[3], h2, dtr;
+    };
+    struct JP {
+        f2 xh[3], m, xl[3], v[3];
+    };
+    template <int NP>
+    static __device__ __forceinline__ void load_j(JP &s, const unsigned char *st, int pl)
+    {
+        const ulonglong2 *q = reinterpret_cast<const ulonglong2 *>(st);
+        const ulonglong2 a = q[pl], b = q[NP + pl], c = q[2 * NP + pl], d = q[3 * NP + pl];
+        const ulonglong2 e = q[4 * NP + pl];
+        s.xh[0] = a.x; s.xh[1] = a.y; s.xh[2] = b.x; s.m = b.y;
+        s.xl[0] = c.x; s.xl[1] = c.y; s.xl[2] = d.x;
+        s.v[0] = d.y; s.v[1] = e.x; s.v[2] = e.y;
+    }
+    static __device__ __forceinline__ void mask(JP &s, bool va, bool vb)
+    {
+        auto fix = [&](f2 &v, float far) {
+            float a, b;
+            up(v, a, b);
+            v = pk(va ? a : far, vb ? b : far);
+        };
+        for (int c = 0; c < 3; c++) {
+            fix(s.xh[c], FAR_F);
+            fix(s.xl[c], 0.f);
+            fix(s.v[c], 0.f);
+        }
+        fix(s.m, 0.f);
+    }
+    static __device__ __forceinline__ void set_i(IB &ib, const JSet &soa, int64_t slot, float h2, float dtr,
+                                                 const Frame2 &)
+    {
+        FormMixed::IS a;
+        FormMixed::clear_i(a);
+        if (slot >= 0) FormMixed::load_i(a, soa, slot);
+        for (int c = 0; c < 3; c++) {
+            ib.nxh[c] = bc(-a.xh[c]);
+            ib.nxl[c] = bc(-a.xl[c]);
+            ib.nv[c] = bc(-a.vh[c]);
+        }
+        ib.h2 = bc(h2);
+        ib.dtr = bc(dtr);
+    }
+    static __device__ __forceinline__ void diffs(const IB &i, const JP &j, f2 &dx, f2 &dy, f2 &dz, f2 &ux, f2 &uy,
+                                                 f2 &uz)
+    {
+        dx = add2(add2(j.xh[0], i.nxh[0]), add2(j.xl[0], i.nxl[0]));
+        dy = add2(add2(j.xh[1], i.nxh[1]), add2(j.xl[1], i.nxl[1]));
+        dz = add2(add2(j.xh[2], i.nxh[2]), add2(j.xl[2], i.nxl[2]));
+        ux = add2(j.v[0], i.nv[0]);
+        uy = add2(j.v[1], i.nv[1]);
+        uz = add2(j.v[2], i.nv[2]);
+    }
+    template <bool VC, bool POT>
+    static __device__ __forceinline__ bool pair(const IB &i, const JP &j, Acc2 &a)
+    {
+        f2 dx, dy, dz, ux, uy, uz;
+        diffs(i, j, dx, dy, dz, ux, uy, uz);
+        return tail2_any<VC, POT>(i.h2, i.dtr, j.m, dx, dy, dz, ux, uy, uz, a);
+    }
+    template <bool VC>
+    static __device__ __forceinline__ void test(const IB &i, const JP &j, bool &fa, bool &fb)
+    {
+        f2 dx, dy, dz, ux, uy, uz;
+        diffs(i, j, dx, dy, dz, ux, uy, uz);
+        test2<VC>(i.h2, i.dtr, dx, dy, dz, ux, uy, uz, fa, fb);
+    }
+};
+
 // Plain FP32 form, pair-interleaved: 4 float4 streams per j-pair
 //   q0 (x_a, x_b, y_a, y_b)  q1 (z_a, z_b, m_a, m_b)  q2 (vx_a, vx_b, vy_a, vy_b)  q3 (vz_a, vz_b, 0, 0)
 struct PairFP32 {

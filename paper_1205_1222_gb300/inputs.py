@@ -260,7 +260,7 @@ def _cache_dir():
 
 
 def cluster(n, seed, k_nb, cap, dt_mode="hierarchy", dt_fixed=2.0**-10, masses="equal",
-            offset=0.0, pair_frac=0.0, act=None, accel=None, dtr_steps=None, name=None):
+            offset=0.0, pair_frac=0.0, act=None, accel=None, dtr_steps=None, name=None, bulk_v=None):
     """One Plummer cluster at block time t = 2 with per-particle radii.
 
     n          particles; seed: PCG64 seed
@@ -273,6 +273,7 @@ def cluster(n, seed, k_nb, cap, dt_mode="hierarchy", dt_fixed=2.0**-10, masses="
     act        active indices (default: all particles)
     accel      None (Plummer field) or a callable (X, V, m) -> (a0, adot0)
     dtr_steps  None (plain criterion) or a tuple of regular steps drawn per particle
+    bulk_v     None or a velocity (3-vector) added to every particle
     """
     rng = np.random.default_rng(np.random.PCG64(seed))
     X, V = plummer(n, rng)
@@ -283,6 +284,8 @@ def cluster(n, seed, k_nb, cap, dt_mode="hierarchy", dt_fixed=2.0**-10, masses="
         meta.update(pair_primary=prim, pair_secondary=sec, pair_sep=sep)
     if offset:
         X += offset / math.sqrt(3.0)
+    if bulk_v is not None:
+        V = V + np.asarray(bulk_v, dtype=np.float64)
     if dt_mode == "fixed":
         dt = np.full(n, dt_fixed)
     else:

@@ -405,10 +405,25 @@ def test_framed_two_float_kernel(offset, pairs):
     compare(g, oracle_run(w), w.cap, "mixed")
 
 
-def test_framed_kernel_is_the_default_for_large_active_sets(cfg2):
+def test_default_mixed_kernel_is_two_float_positions(cfg2):
+    """Unless configured otherwise, two-float calls run the j-pair kernel with
+    two-float positions and FP32 velocity differences (tiling packed = 5)."""
     with Context(cfg2.n) as ctx:
         g = gpu_run(cfg2, "mixed", ctx=ctx)
-        compact, blocks = B.nb_debug_frame_stats(ctx.h)
-    assert blocks > 0 and compact > 0
-    assert g["launches"] > 2          # the sort kernels ran
+        assert ctx.active_config("mixed").packed == 5
+    assert g["launches"] <= 2          # the force kernel (and the merge of j-splits), no sort
     compare(g, oracle_run(cfg2), cfg2.cap, "mixed")
+
+
+@pytest.mark.parametrize("bulk", [1.0, 4.0])
+def test_two_float_positions_with_bulk_velocity(bulk):
+    """FP32 velocity differences round u (|v_i| + |v_j|): a bulk velocity of a
+    few times the dispersion (~0.7 in these units) still meets the two-float
+    tolerances; the exact pair form (packed = 2) does at any bulk velocity."""
+    u = np.array([1.0, -0.5, 0.25])
+    w = inputs.cluster(8192, 37, 64, 256, bulk_v=bulk * u / np.linalg.norm(u))
+    o = oracle_run(w)
+    for packed in (5, 2):
+        g = gpu_run(w, "mixed", cfg=B.nb_kcfg(16, 2, 512, 0, packed))
+        assert g["status"] == 0
+        compare(g, o, w.cap, "mixed")
