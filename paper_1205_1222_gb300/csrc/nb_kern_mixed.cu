@@ -9,11 +9,13 @@
 namespace nb {
 
 static const KernelEntry g_mixed[] = {
+    NB_KERNEL_ENTRY5(16, 2, 1024, 4, 0, 1),
+    NB_KERNEL_ENTRY5(16, 2, 1024, 4, 1, 1),
+    NB_KERNEL_ENTRY5(16, 2, 1024, 4, 2, 1),
+    NB_KERNEL_ENTRY5(16, 2, 1024, 4, 3, 1),
+    NB_KERNEL_ENTRY5(12, 2, 1024, 4, 0, 1),
     NB_KERNEL_ENTRY5(16, 2, 512, 4, 0, 1),
-    NB_KERNEL_ENTRY5(16, 2, 512, 4, 1, 1),
-    NB_KERNEL_ENTRY5(16, 2, 512, 4, 2, 1),
-    NB_KERNEL_ENTRY5(16, 2, 512, 4, 3, 1),
-    NB_KERNEL_ENTRY5(12, 2, 512, 4, 0, 1),
+    NB_KERNEL_ENTRY5(16, 2, 1536, 2, 0, 1),
     NB_KERNEL_ENTRY3(PairMixed, 1, 16, 2, 512, 4, 1, 0, 1),
     NB_KERNEL_ENTRY3(PairMixed, 1, 16, 2, 512, 4, 1, 1, 1),
     NB_KERNEL_ENTRY3(PairMixed, 1, 16, 2, 512, 4, 1, 2, 1),

@@ -101,35 +101,16 @@ __device__ __forceinline__ void tail2(f2 h2, f2 dtr, f2 m, f2 dx, f2 dy, f2 dz, 
     if (POT) a.p = add2(a.p, mr);
 }
 
-// As tail2, but returns only whether either half is a neighbour; the j-pair
-// kernels recompute the individual tests (test2) on the rare steps that have
-// one, with the same operations, so fewer predicates stay live.
-template <bool VC, bool POT>
-__device__ __forceinline__ bool tail2_any(f2 h2, f2 dtr, f2 m, f2 dx, f2 dy, f2 dz, f2 ux, f2 uy, f2 uz, Acc2 &a)
+// Warp-wide OR and lowest set bit of the per-lane neighbour flags of a tile.
+__device__ __forceinline__ uint32_t reduce_or_bits(uint32_t b) { return __reduce_or_sync(0xffffffffu, b); }
+__device__ __forceinline__ uint64_t reduce_or_bits(uint64_t b)
 {
-    bool fa, fb;
-    tail2<VC, POT>(h2, dtr, m, dx, dy, dz, ux, uy, uz, a, fa, fb);
-    return fa | fb;
+    const uint32_t lo = __reduce_or_sync(0xffffffffu, static_cast<uint32_t>(b));
+    const uint32_t hi = __reduce_or_sync(0xffffffffu, static_cast<uint32_t>(b >> 32));
+    return (static_cast<uint64_t>(hi) << 32) | lo;
 }
-
-// The neighbour test of tail2 alone (same operations, so the same decisions).
-template <bool VC>
-__device__ __forceinline__ void test2(f2 h2, f2 dtr, f2 dx, f2 dy, f2 dz, f2 ux, f2 uy, f2 uz, bool &fa, bool &fb)
-{
-    const f2 r2 = fma2(dz, dz, fma2(dy, dy, mul2(dx, dx)));
-    float qa, qb, ha, hb;
-    up(r2, qa, qb);
-    if (VC) {
-        const f2 px = fma2(dtr, ux, dx), py = fma2(dtr, uy, dy), pz = fma2(dtr, uz, dz);
-        float pa, pb;
-        up(fma2(pz, pz, fma2(py, py, mul2(px, px))), pa, pb);
-        qa = fminf(qa, pa);
-        qb = fminf(qb, pb);
-    }
-    up(h2, ha, hb);
-    fa = qa < ha;
-    fb = qb < hb;
-}
+__device__ __forceinline__ int lowest_bit(uint32_t b) { return __ffs(b) - 1; }
+__device__ __forceinline__ int lowest_bit(uint64_t b) { return __ffsll(static_cast<long long>(b)) - 1; }
 
 // Position in the CTA's sequence of j-tiles: the work item, the tile in it,
 // the item's tile end, and the j-range the copies read.

@@ -14,13 +14,13 @@
 // itself out of the stage on a shared counter; the last warp out refills the
 // stage with the tile NSTAGE steps ahead (every warp tracks that look-ahead
 // position), so warps drift freely within the ring.  Per-lane float-float
-// totals live in shared memory (folded every FOLD_STEPS steps), leaving the
+// totals live in shared memory (folded every FOLD_STEPS_J / _F steps), leaving the
 // register file to the i-values and the FP32 partial sums.  The pair terms of
-// a tile run as straight-line code that only marks, per i-particle, which
-// 64-j units held a neighbour; after the tile the lists are compacted from the
-// marked units with ballot + popc over the interleaved (lane, half) order,
-// which is ascending j, the neighbour test being recomputed by the same
-// operations.
+// a tile run as straight-line code that only records, per i-particle, the
+// neighbour flags of the lane's two j in each 64-j unit (two bits per unit);
+// after the tile the lists are compacted from the flagged units with ballot +
+// popc over the interleaved (lane, half) order, which is ascending j, so the
+// list holds exactly the pairs that the force sums left out.
 #pragma once
 
 #include <cfloat>
@@ -102,18 +102,11 @@ struct PairMixed {
         uz = add2(add2(j.vh[2], i.nvh[2]), add2(j.vl[2], i.nvl[2]));
     }
     template <bool VC, bool POT>
-    static __device__ __forceinline__ bool pair(const IB &i, const JP &j, Acc2 &a)
+    static __device__ __forceinline__ void pair(const IB &i, const JP &j, Acc2 &a, bool &fa, bool &fb)
     {
         f2 dx, dy, dz, ux, uy, uz;
         diffs(i, j, dx, dy, dz, ux, uy, uz);
-        return tail2_any<VC, POT>(i.h2, i.dtr, j.m, dx, dy, dz, ux, uy, uz, a);
-    }
-    template <bool VC>
-    static __device__ __forceinline__ void test(const IB &i, const JP &j, bool &fa, bool &fb)
-    {
-        f2 dx, dy, dz, ux, uy, uz;
-        diffs(i, j, dx, dy, dz, ux, uy, uz);
-        test2<VC>(i.h2, i.dtr, dx, dy, dz, ux, uy, uz, fa, fb);
+        tail2<VC, POT>(i.h2, i.dtr, j.m, dx, dy, dz, ux, uy, uz, a, fa, fb);
     }
 };
 
@@ -182,18 +175,11 @@ struct PairMixedX {
         uz = add2(j.v[2], i.nv[2]);
     }
     template <bool VC, bool POT>
-    static __device__ __forceinline__ bool pair(const IB &i, const JP &j, Acc2 &a)
+    static __device__ __forceinline__ void pair(const IB &i, const JP &j, Acc2 &a, bool &fa, bool &fb)
     {
         f2 dx, dy, dz, ux, uy, uz;
         diffs(i, j, dx, dy, dz, ux, uy, uz);
-        return tail2_any<VC, POT>(i.h2, i.dtr, j.m, dx, dy, dz, ux, uy, uz, a);
-    }
-    template <bool VC>
-    static __device__ __forceinline__ void test(const IB &i, const JP &j, bool &fa, bool &fb)
-    {
-        f2 dx, dy, dz, ux, uy, uz;
-        diffs(i, j, dx, dy, dz, ux, uy, uz);
-        test2<VC>(i.h2, i.dtr, dx, dy, dz, ux, uy, uz, fa, fb);
+        tail2<VC, POT>(i.h2, i.dtr, j.m, dx, dy, dz, ux, uy, uz, a, fa, fb);
     }
 };
 
@@ -242,17 +228,10 @@ struct PairFP32 {
         ib.dtr = bc(dtr);
     }
     template <bool VC, bool POT>
-    static __device__ __forceinline__ bool pair(const IB &i, const JP &j, Acc2 &a)
+    static __device__ __forceinline__ void pair(const IB &i, const JP &j, Acc2 &a, bool &fa, bool &fb)
     {
-        return tail2_any<VC, POT>(i.h2, i.dtr, j.m, add2(j.x[0], i.nx[0]), add2(j.x[1], i.nx[1]),
-                                  add2(j.x[2], i.nx[2]), add2(j.v[0], i.nv[0]), add2(j.v[1], i.nv[1]),
-                                  add2(j.v[2], i.nv[2]), a);
-    }
-    template <bool VC>
-    static __device__ __forceinline__ void test(const IB &i, const JP &j, bool &fa, bool &fb)
-    {
-        test2<VC>(i.h2, i.dtr, add2(j.x[0], i.nx[0]), add2(j.x[1], i.nx[1]), add2(j.x[2], i.nx[2]),
-                  add2(j.v[0], i.nv[0]), add2(j.v[1], i.nv[1]), add2(j.v[2], i.nv[2]), fa, fb);
+        tail2<VC, POT>(i.h2, i.dtr, j.m, add2(j.x[0], i.nx[0]), add2(j.x[1], i.nx[1]), add2(j.x[2], i.nx[2]),
+                       add2(j.v[0], i.nv[0]), add2(j.v[1], i.nv[1]), add2(j.v[2], i.nv[2]), a, fa, fb);
     }
 };
 
@@ -388,8 +367,15 @@ __global__ void __launch_bounds__(W * 32, MINB) regf3_kernel(const RegfParams p)
     constexpr int NST = L::NST;
     constexpr int NP = L::NP;
     constexpr int STEPS = NP / 32;                                // a step covers 64 j
-    constexpr int FOLD_STEPS = 64;                                // steps (128 j per lane) per FP32 partial
-    constexpr int FOLD_TILES = STEPS >= FOLD_STEPS ? 1 : FOLD_STEPS / STEPS;
+    // Steps (128 j per lane) per FP32 partial of the jerk, and of the force and
+    // potential: the jerk sum cancels far more (|J| can be ~1e-3 of the sum of
+    // its terms' magnitudes), so its partials are folded into the float-float
+    // totals more often.
+    constexpr int FOLD_STEPS_J = 64, FOLD_STEPS_F = 256;
+    constexpr int FOLD_TILES_J = STEPS >= FOLD_STEPS_J ? 1 : FOLD_STEPS_J / STEPS;
+    constexpr int FOLD_TILES_F = STEPS >= FOLD_STEPS_F ? 1 : FOLD_STEPS_F / STEPS;
+    using Bits = typename std::conditional<2 * STEPS <= 32, uint32_t, uint64_t>::type;
+    static_assert(2 * STEPS <= 64, "two neighbour flags per unit of a tile fit 64 bits");
 
     extern __shared__ __align__(128) unsigned char smem[];
     uint64_t *full = reinterpret_cast<uint64_t *>(smem);          // tile landed (TMA)
@@ -492,9 +478,10 @@ __global__ void __launch_bounds__(W * 32, MINB) regf3_kernel(const RegfParams p)
             const int count = min(JT, d.n_j - jt0);
 
             // Pair terms of the whole tile: U j-pairs per lane per step (U * 64
-            // consecutive j for the warp), no branch; a neighbour in unit
-            // (pair-step k*U+u, i-particle q) only sets bit k*U+u of bits[q].
-            uint32_t bits[I];
+            // consecutive j for the warp), no branch; the neighbour flags of
+            // unit (pair-step) k*U+u and i-particle q go to bits 2(k*U+u) (first
+            // particle of the lane's pair) and 2(k*U+u)+1 (second) of bits[q].
+            Bits bits[I];
 #pragma unroll
             for (int q = 0; q < I; q++) bits[q] = 0u;
             auto step = [&](int k, auto tail_c) {
@@ -506,8 +493,12 @@ __global__ void __launch_bounds__(W * 32, MINB) regf3_kernel(const RegfParams p)
                     P::template load_j<NP>(jp, st, pl);
                     if (tail) P::mask(jp, 2 * pl < count, 2 * pl + 1 < count);
 #pragma unroll
-                    for (int q = 0; q < I; q++)
-                        if (P::template pair<VC, POT>(ipart[q], jp, acc[q])) bits[q] |= 1u << (k * U + u);
+                    for (int q = 0; q < I; q++) {
+                        bool fa, fb;
+                        P::template pair<VC, POT>(ipart[q], jp, acc[q], fa, fb);
+                        const int b = 2 * (k * U + u);
+                        bits[q] |= (fa ? Bits(1) << b : Bits(0)) | (fb ? Bits(2) << b : Bits(0));
+                    }
                 }
             };
             if (count == JT) {
@@ -521,16 +512,12 @@ __global__ void __launch_bounds__(W * 32, MINB) regf3_kernel(const RegfParams p)
             // the flagged units in order; within a unit the order is (lane, half).
 #pragma unroll
             for (int q = 0; q < I; q++) {
-                uint32_t todo = __reduce_or_sync(0xffffffffu, bits[q]);
+                Bits todo = reduce_or_bits(bits[q]);
                 while (todo) {
-                    const int unit = __ffs(todo) - 1;
-                    todo &= todo - 1;
+                    const int unit = lowest_bit(todo) >> 1;
+                    todo &= ~(Bits(3) << (2 * unit));
                     const int pl = unit * 32 + lane;
-                    JP jp;
-                    P::template load_j<NP>(jp, st, pl);
-                    if (count < JT) P::mask(jp, 2 * pl < count, 2 * pl + 1 < count);
-                    bool fa, fb;
-                    P::template test<VC>(ipart[q], jp, fa, fb);
+                    const bool fa = (bits[q] >> (2 * unit)) & 1u, fb = (bits[q] >> (2 * unit + 1)) & 1u;
                     const int ja = jt0 + 2 * pl;
                     const int gq = mygi[q];
                     const bool xa = fa && ja != gq, xb = fb && ja + 1 != gq;
@@ -568,21 +555,28 @@ __global__ void __launch_bounds__(W * 32, MINB) regf3_kernel(const RegfParams p)
                 }
             }
             cursor_next(p, la);
-            if ((t - tb + 1) % FOLD_TILES == 0 || t + 1 == te) {
+            auto fold = [&](int c) {
 #pragma unroll
                 for (int q = 0; q < I; q++) {
-#pragma unroll
-                    for (int c = 0; c < NC; c++) {
-                        f2 &part = c < 3 ? acc[q].f[c] : (c < 6 ? acc[q].j[c - 3] : acc[q].p);
-                        float2 *slot = mytot + (q * NC + c) * 32;
-                        float2 v = *slot;
-                        float pa, pb;
-                        up(part, pa, pb);
-                        ff_add(v.x, v.y, pa + pb);   // the two halves' partials first, then TwoSum
-                        *slot = v;
-                        part = 0ull;
-                    }
+                    f2 &part = c < 3 ? acc[q].f[c] : (c < 6 ? acc[q].j[c - 3] : acc[q].p);
+                    float2 *slot = mytot + (q * NC + c) * 32;
+                    float2 v = *slot;
+                    float pa, pb;
+                    up(part, pa, pb);
+                    ff_add(v.x, v.y, pa + pb);   // the two halves' partials first, then TwoSum
+                    *slot = v;
+                    part = 0ull;
                 }
+            };
+            const bool last = t + 1 == te;
+            if ((t - tb + 1) % FOLD_TILES_J == 0 || last) {
+#pragma unroll
+                for (int c = 3; c < 6; c++) fold(c);
+            }
+            if ((t - tb + 1) % FOLD_TILES_F == 0 || last) {
+#pragma unroll
+                for (int c = 0; c < 3; c++) fold(c);
+                if (POT) fold(6);
             }
         }
         if (aborted) return;
