@@ -508,6 +508,22 @@ __global__ void __launch_bounds__(W * 32, MINB) regf3_kernel(const RegfParams p)
 #pragma unroll 1
                 for (int k = 0; k < STEPS / U; ++k) step(k, std::true_type{});
             }
+            // count this warp out of the stage (the list pass below reads only the
+            // flags); the last one refills it NST tiles ahead
+            __syncwarp();
+            if (lane == 0) {
+                __threadfence_block();
+                if (atomicAdd(&rel[s], 1) == W - 1) {
+                    rel[s] = 0;
+                    if constexpr (FRAMED) {
+                        claim[s] = 0;
+                        fence_proxy_async_smem();   // the stage was written through the generic proxy
+                    }
+                    if (la.item < p.n_items) issue_pairs<Fm, JT, NST>(p, la, g + NST, full, stages);
+                }
+            }
+            cursor_next(p, la);
+
             // Neighbour lists of the tile, in ascending j: for each i-particle,
             // the flagged units in order; within a unit the order is (lane, half).
 #pragma unroll
@@ -541,20 +557,6 @@ __global__ void __launch_bounds__(W * 32, MINB) regf3_kernel(const RegfParams p)
                 }
             }
 
-            // count this warp out of the stage; the last one refills it NST tiles ahead
-            __syncwarp();
-            if (lane == 0) {
-                __threadfence_block();
-                if (atomicAdd(&rel[s], 1) == W - 1) {
-                    rel[s] = 0;
-                    if constexpr (FRAMED) {
-                        claim[s] = 0;
-                        fence_proxy_async_smem();   // the stage was written through the generic proxy
-                    }
-                    if (la.item < p.n_items) issue_pairs<Fm, JT, NST>(p, la, g + NST, full, stages);
-                }
-            }
-            cursor_next(p, la);
             auto fold = [&](int c) {
 #pragma unroll
                 for (int q = 0; q < I; q++) {
