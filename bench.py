@@ -53,7 +53,8 @@ def parse_args():
     ap.add_argument("--cpu-sample", type=int, default=4096, help="active particles in the oracle sample")
     ap.add_argument("--no-e2e", action="store_true", help="skip the host-buffer measurement")
     ap.add_argument("--config", default="", help="kernel tiling warps,ipw,jtile,packed[,split] "
-                                                 "(default: the library's default for the mode)")
+                                                 "(default: the autotuner's choice)")
+    ap.add_argument("--no-tune", action="store_true", help="skip the autotuner (library default tiling)")
     ap.add_argument("--n", type=int, default=131072,
                     help="j-particles (131072 = the benchmark workload; smaller N builds the same kind of "
                          "cluster, used for profiling captures)")
@@ -263,6 +264,24 @@ class Runner:
         force_ms = [e[1].elapsed_time(e[2]) for e in ev]
         return step_ms, force_ms
 
+    def autotune(self, reps=1):
+        """Native autotuner on this workload (untimed); later calls use its choice."""
+        from paper_1205_1222_gb300 import autotune
+        self.predict()
+        t0 = time.perf_counter()
+        best, ms = self.ctx.autotune(self.d["act"], self.d["h"], self.w.n, cap=self.w.cap, mode=self.mode,
+                                     out=self.out, reps=reps, stream=self.stream)
+        self.cfg = best.as_tuple()
+        return {"best": list(self.cfg), "best_ms": ms, "seconds": time.perf_counter() - t0,
+                "table": autotune.table(self.ctx)}
+
+    def load_tuned(self, rows):
+        for r in rows:
+            t = self.B.nb_tuned()
+            t.mode, t.flags, t.act_class, t.j_class = r["mode"], r["flags"], r["act_class"], r["j_class"]
+            t.cfg = self.B.nb_kcfg(*r["cfg"])
+            self.B.nb_set_tuned(self.ctx.h, t)
+
     def outputs(self):
         return {k: v.cpu().numpy() for k, v in self.out.items() if v is not None}
 
@@ -270,7 +289,7 @@ class Runner:
         self.ctx.close()
 
 
-def e2e_measure(w, mode, device, steps):
+def e2e_measure(w, mode, device, steps, tuned=()):
     """The same step through nb_step_host: host (pinned) inputs in, host outputs out."""
     import numpy as np
     import torch
@@ -288,6 +307,11 @@ def e2e_measure(w, mode, device, steps):
     d2h = sum(t.numel() * t.element_size() for t in (F, J, nnb, lst, ovf))
     with Context(w.n, device=device) as ctx:
         st = torch.cuda.current_stream(device)
+        for r in tuned:
+            t = B.nb_tuned()
+            t.mode, t.flags, t.act_class, t.j_class = r["mode"], r["flags"], r["act_class"], r["j_class"]
+            t.cfg = B.nb_kcfg(*r["cfg"])
+            B.nb_set_tuned(ctx.h, t)
 
         def step():
             B.nb_step_host(ctx.h, w.n, hx["x0"], hx["v0"], hx["a0"], hx["adot0"], hx["m"], hx["t0"], w.t, w.n_act,
@@ -355,6 +379,9 @@ def run_ours(args):
         torch.distributed.barrier()
     w = workload(args.n_act, args.n)
     r = Runner(w, args.mode, device, args.config)
+    tune = None
+    if not args.config and not args.no_tune and args.mode != "fp64":
+        tune = r.autotune()
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=f"cuda:{device}")
     for _ in range(max(args.warmup, 3)):
         r.predict()
@@ -419,6 +446,10 @@ def run_ours(args):
     if clk:
         line["roofline"]["peak_at_measured_clock"] = fp32_peak_tflops(sm, clk["sm_mhz"])
         line["roofline"]["frac_at_measured_clock"] = achieved / line["roofline"]["peak_at_measured_clock"]
+    if tune:
+        line["autotune"] = {"chosen": tune["best"], "best_ms": tune["best_ms"], "seconds": tune["seconds"],
+                            "note": "native nb_autotune over every compiled tiling and j-split, before the "
+                                    "timed region"}
     line["gpu_launches"] = launches
     line["clocks"] = clk
     if remeasured:
@@ -432,9 +463,11 @@ def run_ours(args):
         for label, mode, cfg in (("fp64", "fp64", ""), ("fp32", "fp32", ""), ("mixed", "mixed", ""),
                                  ("mixed_exact_pair", "mixed", "16,2,512,2")):
             if mode == args.mode and not cfg and not args.config:
-                forms[label] = {"value": value / world, "ms_per_step": ms, "kernel_ms": fms}
+                forms[label] = {"value": value / world, "ms_per_step": ms, "kernel_ms": fms, "tiling": r.cfg}
                 continue
             rr = Runner(w, mode, device, cfg)
+            if mode == "fp32" and not args.no_tune:
+                rr.autotune()
             rr.predict(); rr.force()
             torch.cuda.synchronize(device)
             k = 2 if mode == "fp64" else args.steps
@@ -446,7 +479,7 @@ def run_ours(args):
             rr.close()
         line["forms"] = forms
     if not args.no_e2e:
-        line["e2e"] = e2e_measure(w, args.mode, device, max(1, min(args.steps, 5)))
+        line["e2e"] = e2e_measure(w, args.mode, device, max(1, min(args.steps, 5)), tune["table"] if tune else ())
     if not args.no_cpu_baseline:
         base, o, rows = cpu_baseline(w, args.cpu_sample)
         line["cpu_baseline"] = base

@@ -248,6 +248,37 @@ int nb_time_regular_force(nb_ctx *ctx, const nb_kcfg *cfg, int64_t j_begin, int6
                           double *pot, int32_t *nnb, int32_t *list, uint8_t *ovf, int reps,
                           nb_stream_t stream, float *ms);
 
+/* Autotuner.  A call's size class is (mode, flags, floor(log2 n_act),
+ * floor(log2 n_j)), flags = 1 with a velocity criterion (dtr != NULL) | 2 with
+ * a potential output.  nb_autotune times, on the caller's own call (the same
+ * arguments as nb_regular_force; its outputs are overwritten), every compiled
+ * tiling of the mode with exactly those flags, each with the default j-split
+ * and with j-splits that give about 1, 2, 4 and 8 work items per resident CTA
+ * and one split only, `reps` calls per candidate after one warm-up, and keeps
+ * the fastest for the call's size class in the context.  Later calls of that
+ * class (nb_regular_force, nb_step_host, nb_plan_create with the summed n_act
+ * and the largest n_j) use the tuned tiling unless nb_set_kernel_config chose
+ * one.  *best and *best_ms (either may be NULL) receive the winner and its
+ * mean time.  Synchronises with the device.  Not a step of the paper's method:
+ * it picks the i-tile, j-tile and j-split of the kernels. */
+typedef struct {
+    int32_t mode, flags, act_class, j_class;
+    nb_kcfg cfg;
+    float ms; /* mean device time per call measured by nb_autotune (0 if loaded) */
+} nb_tuned;
+int nb_autotune(nb_ctx *ctx, int64_t j_begin, int64_t n_j, int32_t n_act, const int32_t *act,
+                const double *h, const double *dtr, int32_t cap, int mode, double *F, double *J,
+                double *pot, int32_t *nnb, int32_t *list, uint8_t *ovf, int reps,
+                nb_stream_t stream, nb_kcfg *best, float *best_ms);
+/* The context's tuned table: entry count, entry `index` (in key order), and
+ * insertion of an entry (e.g. one saved by an earlier run).  nb_set_tuned
+ * checks that a kernel with the entry's tiling and flags is compiled
+ * (NB_ERR_UNSUPPORTED otherwise); an entry with cfg.warps == 0 removes its
+ * class from the table. */
+int nb_num_tuned(nb_ctx *ctx);
+int nb_get_tuned(nb_ctx *ctx, int index, nb_tuned *out);
+int nb_set_tuned(nb_ctx *ctx, const nb_tuned *entry);
+
 /* Number of kernels the last nb_regular_force call on this context launched. */
 int nb_last_launches(nb_ctx *ctx);
 

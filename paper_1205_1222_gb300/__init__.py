@@ -94,3 +94,12 @@ class Context:
 
     def active_config(self, mode):
         return _b.nb_get_active_config(self.h, mode_id(mode))
+
+    def autotune(self, act, h, n_j, dtr=None, cap=256, mode="mixed", j_begin=0, pot=False, out=None,
+                 reps=3, stream=None):
+        """Tune the tiling for this call's size class (native nb_autotune);
+        returns (best nb_kcfg, mean ms per call).  Overwrites `out`."""
+        n_act = int(act.shape[0])
+        out = out or self.alloc_outputs(n_act, cap, pot)
+        return _b.nb_autotune(self.h, j_begin, n_j, n_act, act, h, dtr, cap, mode_id(mode), out["F"], out["J"],
+                              out["pot"], out["nnb"], out["list"], out["ovf"], reps, stream)

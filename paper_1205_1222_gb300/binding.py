@@ -37,6 +37,7 @@ EXPORTS = [
     "nb_strerror", "nb_last_error", "nb_num_kernel_configs", "nb_get_kernel_config",
     "nb_set_kernel_config", "nb_get_active_config", "nb_time_regular_force", "nb_last_launches",
     "nb_sm_count", "nb_debug_set_wait", "nb_regular_force_noalloc", "nb_debug_frame_stats",
+    "nb_autotune", "nb_num_tuned", "nb_get_tuned", "nb_set_tuned",
 ]
 
 
@@ -55,6 +56,11 @@ class nb_kcfg(ctypes.Structure):
 
     def __repr__(self):
         return "nb_kcfg(warps=%d, ipw=%d, jtile=%d, split=%d, packed=%d)" % self.as_tuple()
+
+
+class nb_tuned(ctypes.Structure):
+    _fields_ = [("mode", ctypes.c_int32), ("flags", ctypes.c_int32), ("act_class", ctypes.c_int32),
+                ("j_class", ctypes.c_int32), ("cfg", nb_kcfg), ("ms", ctypes.c_float)]
 
 
 class nb_cluster(ctypes.Structure):
@@ -107,6 +113,11 @@ def library():
         "nb_debug_set_wait": ([P, ctypes.c_uint64, ctypes.c_uint32], cint),
         "nb_debug_frame_stats": ([P, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int)], cint),
         "nb_regular_force_noalloc": ([P, i64, i64, i32, P, P, P, i32, cint, P, P, P, P, P, P, P], cint),
+        "nb_autotune": ([P, i64, i64, i32, P, P, P, i32, cint, P, P, P, P, P, P, cint, P,
+                         ctypes.POINTER(nb_kcfg), ctypes.POINTER(ctypes.c_float)], cint),
+        "nb_num_tuned": ([P], cint),
+        "nb_get_tuned": ([P, cint, ctypes.POINTER(nb_tuned)], cint),
+        "nb_set_tuned": ([P, ctypes.POINTER(nb_tuned)], cint),
     }
     for name, (args, res) in sig.items():
         f = getattr(lib, name)
@@ -244,6 +255,30 @@ def nb_time_regular_force(ctx, cfg, j_begin, n_j, n_act, act, h, dtr, cap, mode,
                                                 _stream(stream), ctypes.byref(ms)),
            "nb_time_regular_force")
     return float(ms.value)
+
+
+def nb_autotune(ctx, j_begin, n_j, n_act, act, h, dtr, cap, mode, F, J, pot, nnb, lst, ovf, reps=3,
+                stream=None):
+    best = nb_kcfg()
+    ms = ctypes.c_float()
+    _check(ctx, library().nb_autotune(ctx, int(j_begin), int(n_j), int(n_act), _p(act), _p(h), _p(dtr), int(cap),
+                                      int(mode), _p(F), _p(J), _p(pot), _p(nnb), _p(lst), _p(ovf), int(reps),
+                                      _stream(stream), ctypes.byref(best), ctypes.byref(ms)),
+           "nb_autotune")
+    return best, float(ms.value)
+
+
+def nb_tuned_table(ctx):
+    out = []
+    for i in range(int(library().nb_num_tuned(ctx))):
+        t = nb_tuned()
+        _check(ctx, library().nb_get_tuned(ctx, i, ctypes.byref(t)), "nb_get_tuned")
+        out.append(t)
+    return out
+
+
+def nb_set_tuned(ctx, entry):
+    _check(ctx, library().nb_set_tuned(ctx, ctypes.byref(entry)), "nb_set_tuned")
 
 
 def nb_last_launches(ctx):

@@ -8,6 +8,7 @@
 #include <algorithm>
 #include <cstdio>
 #include <cstring>
+#include <map>
 #include <mutex>
 #include <string>
 #include <vector>
@@ -82,6 +83,7 @@ struct nb_ctx {
     size_t scratch_bytes = 0;
     nb_kcfg cfg[3];
     bool cfg_set[3] = {false, false, false};
+    std::map<uint64_t, nb_tuned> tuned;   // autotuner table, by size class
     int last_launches = 0;
     uint64_t wait_ns = kDefaultWaitNs;
     uint32_t extra_tx = 0;
@@ -135,6 +137,28 @@ nb_kcfg default_cfg(int mode)
     for (const auto &e : r.all)
         if (e.mode == mode && e.flags == 0) return nb_kcfg{e.warps, e.ipw, e.jtile, 0, e.packed};
     return nb_kcfg{0, 0, 0, 0, 0};
+}
+
+// Size class of the autotuner: (mode, flags, floor(log2 n_act), floor(log2 n_j)).
+int log2_floor(int64_t n)
+{
+    int c = 0;
+    while (n > 1) { n >>= 1; ++c; }
+    return c;
+}
+uint64_t tune_key(int mode, int flags, int act_class, int j_class)
+{
+    return static_cast<uint64_t>(mode) | static_cast<uint64_t>(flags) << 4 |
+           static_cast<uint64_t>(act_class) << 8 | static_cast<uint64_t>(j_class) << 16;
+}
+
+// Tiling of a call: the one chosen with nb_set_kernel_config, else the tuned
+// one of the call's size class, else the mode's default.
+nb_kcfg pick_cfg(const nb_ctx *ctx, int mode, int flags, int64_t n_act, int64_t n_j)
+{
+    if (ctx->cfg_set[mode]) return ctx->cfg[mode];
+    const auto it = ctx->tuned.find(tune_key(mode, flags, log2_floor(n_act), log2_floor(n_j)));
+    return it != ctx->tuned.end() ? it->second.cfg : default_cfg(mode);
 }
 
 // Index of the kernel for (mode, cfg, flags); falls back to the mode's default
@@ -364,9 +388,8 @@ int run_single(nb_ctx *ctx, const Call &c, const nb_kcfg *cfg_override, cudaStre
     ctx->last_launches = 0;
     if (c.n_act == 0) return NB_OK;
     DeviceGuard guard(ctx->device);
-    const nb_kcfg cfg = cfg_override ? *cfg_override
-                                     : (ctx->cfg_set[c.mode] ? ctx->cfg[c.mode] : default_cfg(c.mode));
     const int flags = (c.dtr ? 1 : 0) | (c.pot ? 2 : 0);
+    const nb_kcfg cfg = cfg_override ? *cfg_override : pick_cfg(ctx, c.mode, flags, c.n_act, c.n_j);
     int idx = find_entry(c.mode, cfg, flags);
     if (idx < 0) { ctx->err = "no kernel for this mode"; return NB_ERR_UNSUPPORTED; }
     if (registry().all[idx].packed >= 2 && (c.j_begin & 1)) idx = layout_fallback(c.mode, idx, flags);
@@ -583,9 +606,9 @@ int nb_reserve(nb_ctx *ctx, size_t bytes)
 size_t nb_scratch_bytes(nb_ctx *ctx, int64_t n_j, int32_t n_act, int32_t cap, int mode)
 {
     if (!ctx || mode < 0 || mode > 2 || n_act <= 0 || n_j <= 0 || cap < 0) return 0;
-    const nb_kcfg cfg = ctx->cfg_set[mode] ? ctx->cfg[mode] : default_cfg(mode);
     size_t best = 0;
     for (int flags = 0; flags < 4; flags++) {   // the largest over the flag variants
+        const nb_kcfg cfg = pick_cfg(ctx, mode, flags, n_act, n_j);
         const int idx = find_entry(mode, cfg, flags);
         if (idx < 0) continue;
         int occ = 0;
@@ -681,6 +704,93 @@ int nb_time_regular_force(nb_ctx *ctx, const nb_kcfg *cfg, int64_t j_begin, int6
     if (e != cudaSuccess) return cuda_fail(ctx, e, "timing events");
     *ms = t / reps;
     return NB_OK;
+}
+
+// ------------------------------------------------------------ autotuner
+
+int nb_autotune(nb_ctx *ctx, int64_t j_begin, int64_t n_j, int32_t n_act, const int32_t *act,
+                const double *h, const double *dtr, int32_t cap, int mode, double *F, double *J,
+                double *pot, int32_t *nnb, int32_t *list, uint8_t *ovf, int reps,
+                nb_stream_t stream, nb_kcfg *best, float *best_ms)
+{
+    if (!ctx || reps <= 0) return NB_ERR_ARG;
+    DeviceGuard guard(ctx->device);
+    const Call c{j_begin, n_j, n_act, act, h, dtr, cap, mode, F, J, pot, nnb, list, ovf};
+    int rc = check_call(ctx, c);
+    if (rc != NB_OK) return rc;
+    if (n_act <= 0) { ctx->err = "nothing to tune (n_act = 0)"; return NB_ERR_ARG; }
+    const int flags = (dtr ? 1 : 0) | (pot ? 2 : 0);
+    Registry &r = registry();
+    nb_kcfg win{0, 0, 0, 0, 0};
+    float win_ms = 0.f;
+    for (size_t i = 0; i < r.all.size(); i++) {
+        const KernelEntry &e = r.all[i];
+        if (e.mode != mode || e.flags != flags) continue;
+        if (e.packed >= 2 && (j_begin & 1)) continue;   // j-pair layouts need an even first slot
+        int occ = 0;
+        rc = entry_occupancy(ctx, static_cast<int>(i), &occ);
+        if (rc != NB_OK) return rc;
+        // j-split candidates: the default, one split, and ~1, 2, 4, 8 items per resident CTA
+        ClusterDesc d{};
+        d.n_j = static_cast<int32_t>(n_j);
+        d.n_act = n_act;
+        d.cap = cap;
+        tile_cluster(e, occ, ctx->sm_count, nullptr, d);
+        std::vector<int> splits{0, d.n_tiles};
+        const int64_t slots = static_cast<int64_t>(ctx->sm_count) * occ;
+        for (int k : {1, 2, 4, 8}) {
+            const int64_t n_split = std::max<int64_t>(1, (k * slots + d.n_iblk - 1) / std::max(d.n_iblk, 1));
+            splits.push_back(static_cast<int>(std::max<int64_t>(1, (d.n_tiles + n_split - 1) / n_split)));
+        }
+        std::vector<int> tried;
+        for (int sp : splits) {
+            const int tps = sp == 0 ? d.tiles_per_split : sp;
+            if (std::find(tried.begin(), tried.end(), tps) != tried.end()) continue;
+            tried.push_back(tps);
+            const nb_kcfg cfg{e.warps, e.ipw, e.jtile, sp, e.packed};
+            float ms = 0.f;
+            rc = nb_time_regular_force(ctx, &cfg, j_begin, n_j, n_act, act, h, dtr, cap, mode, F, J, pot, nnb,
+                                       list, ovf, reps, stream, &ms);
+            if (rc == NB_ERR_NOMEM) continue;   // this split's scratch does not fit: skip it
+            if (rc != NB_OK) return rc;
+            const int st = nb_sync_status(ctx, stream);
+            if (st != NB_OK) return st;
+            if (win.warps == 0 || ms < win_ms) { win = cfg; win_ms = ms; }
+        }
+    }
+    if (win.warps == 0) { ctx->err = "no compiled kernel for this call"; return NB_ERR_UNSUPPORTED; }
+    nb_tuned t{mode, flags, log2_floor(n_act), log2_floor(n_j), win, win_ms};
+    ctx->tuned[tune_key(mode, flags, t.act_class, t.j_class)] = t;
+    if (best) *best = win;
+    if (best_ms) *best_ms = win_ms;
+    return NB_OK;
+}
+
+int nb_num_tuned(nb_ctx *ctx) { return ctx ? static_cast<int>(ctx->tuned.size()) : 0; }
+
+int nb_get_tuned(nb_ctx *ctx, int index, nb_tuned *out)
+{
+    if (!ctx || !out || index < 0 || index >= static_cast<int>(ctx->tuned.size())) return NB_ERR_ARG;
+    auto it = ctx->tuned.begin();
+    std::advance(it, index);
+    *out = it->second;
+    return NB_OK;
+}
+
+int nb_set_tuned(nb_ctx *ctx, const nb_tuned *t)
+{
+    if (!ctx || !t || t->mode < 0 || t->mode > 2 || t->flags < 0 || t->flags > 3 || t->act_class < 0 ||
+        t->act_class > 62 || t->j_class < 0 || t->j_class > 62 || t->cfg.split < 0)
+        return NB_ERR_ARG;
+    const uint64_t key = tune_key(t->mode, t->flags, t->act_class, t->j_class);
+    if (t->cfg.warps == 0) { ctx->tuned.erase(key); return NB_OK; }
+    for (const auto &e : registry().all)
+        if (e.mode == t->mode && e.flags == t->flags && e.warps == t->cfg.warps && e.ipw == t->cfg.ipw &&
+            e.jtile == t->cfg.jtile && e.packed == t->cfg.packed) {
+            ctx->tuned[key] = *t;
+            return NB_OK;
+        }
+    return NB_ERR_UNSUPPORTED;
 }
 
 // ------------------------------------------------------------ host step
@@ -794,14 +904,17 @@ int nb_plan_create(nb_ctx *ctx, int32_t n_clusters, const nb_cluster *cl, int mo
     *out = nullptr;
     DeviceGuard guard(ctx->device);
     int flags = 0;
+    int64_t act_sum = 0, j_max = 1;
     for (int c = 0; c < n_clusters; c++) {
         const Call call{cl[c].j_begin, cl[c].n_j, cl[c].n_act, cl[c].act, cl[c].h, cl[c].dtr, cl[c].cap,
                         mode, cl[c].F, cl[c].J, cl[c].pot, cl[c].nnb, cl[c].list, cl[c].ovf};
         const int rc = check_call(ctx, call);
         if (rc != NB_OK) return rc;
         flags |= (cl[c].dtr ? 1 : 0) | (cl[c].pot ? 2 : 0);
+        act_sum += cl[c].n_act;
+        j_max = std::max<int64_t>(j_max, cl[c].n_j);
     }
-    const nb_kcfg cfg = cfg_in ? *cfg_in : (ctx->cfg_set[mode] ? ctx->cfg[mode] : default_cfg(mode));
+    const nb_kcfg cfg = cfg_in ? *cfg_in : pick_cfg(ctx, mode, flags, std::max<int64_t>(act_sum, 1), j_max);
     int idx = find_entry(mode, cfg, flags);
     if (idx < 0) return NB_ERR_UNSUPPORTED;
     bool odd = false;

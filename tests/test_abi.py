@@ -1,5 +1,6 @@
 """The C-ABI library builds for sm_103a, loads, and exports every declared
 entry point (CPU only: no compute call is made)."""
+import ctypes
 import os
 import re
 import subprocess
@@ -59,3 +60,19 @@ def test_create_without_a_device_fails_cleanly(lib_path):
     with pytest.raises(binding.NbError) as e:
         binding.nb_create(0, 1024)
     assert e.value.status == binding.NB_ERR_ARG
+
+
+def test_tuned_table_calls_reject_a_null_context(lib_path):
+    lib = binding.library()
+    t = binding.nb_tuned()
+    assert lib.nb_num_tuned(None) == 0
+    assert lib.nb_set_tuned(None, ctypes.byref(t)) == binding.NB_ERR_ARG
+    assert lib.nb_get_tuned(None, 0, ctypes.byref(t)) == binding.NB_ERR_ARG
+
+
+def test_tuned_table_file_format_is_checked(tmp_path):
+    from paper_1205_1222_gb300 import autotune
+    p = tmp_path / "t.json"
+    p.write_text('{"format": "something-else", "entries": []}')
+    with pytest.raises(ValueError):
+        autotune.load(None, str(p))
