@@ -55,6 +55,11 @@ def parse_args():
     ap.add_argument("--config", default="", help="kernel tiling warps,ipw,jtile,packed[,split] "
                                                  "(default: the autotuner's choice)")
     ap.add_argument("--no-tune", action="store_true", help="skip the autotuner (library default tiling)")
+    ap.add_argument("--workload", default="headline", choices=["headline", "batched64", "offset-pairs", "velocity"],
+                    help="headline: the benchmark line; batched64: 64 independent clusters, one persistent "
+                         "launch in a CUDA graph vs one launch per cluster; offset-pairs: N=262144 offset "
+                         "cluster with 10%% hard pairs, FP32 vs two-float vs FP64 with errors; velocity: the "
+                         "headline workload with the velocity neighbour criterion")
     ap.add_argument("--n", type=int, default=131072,
                     help="j-particles (131072 = the benchmark workload; smaller N builds the same kind of "
                          "cluster, used for profiling captures)")
@@ -231,6 +236,9 @@ class Runner:
         self.stream = torch.cuda.current_stream(device)
         self.form = B.MODE_FORM[self.mode]
         self.launches = 0
+        self.use_dtr = False
+        if w.dtr is not None:
+            self.d["dtr"] = dv(w.dtr)
         if cfg:
             f = [int(x) for x in cfg.split(",")]
             B.nb_set_kernel_config(self.ctx.h, self.mode, B.nb_kcfg(f[0], f[1], f[2], f[4] if len(f) > 4 else 0,
@@ -245,7 +253,8 @@ class Runner:
 
     def force(self):
         d, o = self.d, self.out
-        self.B.nb_regular_force(self.ctx.h, 0, self.w.n, self.w.n_act, d["act"], d["h"], None, self.w.cap,
+        self.B.nb_regular_force(self.ctx.h, 0, self.w.n, self.w.n_act, d["act"], d["h"],
+                                d["dtr"] if self.use_dtr else None, self.w.cap,
                                 self.mode, o["F"], o["J"], None, o["nnb"], o["list"], o["ovf"], self.stream)
         self.launches += self.ctx.last_launches()
 
@@ -270,6 +279,7 @@ class Runner:
         self.predict()
         t0 = time.perf_counter()
         best, ms = self.ctx.autotune(self.d["act"], self.d["h"], self.w.n, cap=self.w.cap, mode=self.mode,
+                                     dtr=self.d["dtr"] if self.use_dtr else None,
                                      out=self.out, reps=reps, stream=self.stream)
         self.cfg = best.as_tuple()
         return {"best": list(self.cfg), "best_ms": ms, "seconds": time.perf_counter() - t0,
@@ -526,10 +536,192 @@ def run_reference(args):
     print(json.dumps(line), flush=True)
 
 
+# ------------------------------------------------------- side workloads
+
+def _timed_events(fn, steps, flush, stream, torch):
+    ev = [[torch.cuda.Event(enable_timing=True) for _ in range(2)] for _ in range(steps)]
+    for s in range(steps):
+        flush.zero_()
+        ev[s][0].record(stream)
+        fn()
+        ev[s][1].record(stream)
+    torch.cuda.synchronize()
+    return [e[0].elapsed_time(e[1]) for e in ev]
+
+
+def run_batched(args):
+    """64 independent clusters (N log-uniform in [1024, 32768], n_act log-uniform
+    in [8, N]): prediction of all clusters in one launch plus the regular force
+    of all of them as one persistent launch (and the split merge) replayed from
+    a CUDA graph, against one nb_regular_force call per cluster."""
+    import numpy as np
+    import torch
+
+    from paper_1205_1222_gb300 import Context, binding as B, build, inputs, mode_id
+    build.build()
+    torch.cuda.set_device(0)
+    ws = inputs.cached(inputs.config4)
+    offs = np.cumsum([0] + [w.n + (w.n % 2) for w in ws])
+    total = int(offs[-1])
+    # one j-set: clusters at even offsets, padded slots get zero mass far away
+    x0 = np.zeros((total, 3)); v0 = np.zeros((total, 3)); a0 = np.zeros((total, 3)); ad = np.zeros((total, 3))
+    m = np.zeros(total); t0 = np.full(total, ws[0].t)
+    for w, o in zip(ws, offs):
+        x0[o:o + w.n], v0[o:o + w.n], a0[o:o + w.n], ad[o:o + w.n] = w.x0, w.v0, w.a0, w.adot0
+        m[o:o + w.n], t0[o:o + w.n] = w.m, w.t0
+    for o, w in zip(offs, ws):
+        if w.n % 2:
+            x0[o + w.n] = 1e6
+    dev = lambda a, dt=torch.float64: torch.as_tensor(np.ascontiguousarray(a), dtype=dt, device="cuda")
+    mode = mode_id(args.mode)
+    inter = int(sum(w.n * w.n_act for w in ws))
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
+    with Context(total) as ctx:
+        d = {k: dev(v) for k, v in (("x0", x0), ("v0", v0), ("a0", a0), ("ad", ad), ("m", m), ("t0", t0))}
+        keep, cl = [], []
+        for w, o in zip(ws, offs):
+            a, h = dev(w.act, torch.int32), dev(w.h)
+            out = ctx.alloc_outputs(w.n_act, w.cap)
+            keep.append((a, h, out))
+            cl.append(B.nb_cluster(int(o), w.n, w.n_act, w.cap, a.data_ptr(), h.data_ptr(), None,
+                                   out["F"].data_ptr(), out["J"].data_ptr(), None, out["nnb"].data_ptr(),
+                                   out["list"].data_ptr(), out["ovf"].data_ptr()))
+        stream = torch.cuda.Stream()
+        form = B.MODE_FORM[mode]
+
+        def predict():
+            B.nb_predict(ctx.h, 0, total, d["x0"], d["v0"], d["a0"], d["ad"], d["m"], d["t0"], ws[0].t, form, stream)
+
+        with torch.cuda.stream(stream):
+            predict()
+            plan = B.nb_plan_create(ctx.h, cl, mode)
+            try:
+                B.nb_plan_capture(plan, stream=stream, ctx=ctx.h)
+                for _ in range(max(args.warmup, 3)):
+                    predict(); B.nb_plan_launch(plan, stream=stream, ctx=ctx.h)
+                graph_ms = _timed_events(lambda: (predict(), B.nb_plan_launch(plan, stream=stream, ctx=ctx.h)),
+                                         args.steps, flush, stream, torch)
+                plan_launches = 1 + B.nb_plan_launches(plan)
+            finally:
+                B.nb_plan_destroy(plan)
+
+            def per_cluster():
+                predict()
+                for w, o, (a, h, out) in zip(ws, offs, keep):
+                    B.nb_regular_force(ctx.h, int(o), w.n, w.n_act, a, h, None, w.cap, mode, out["F"], out["J"],
+                                       None, out["nnb"], out["list"], out["ovf"], stream)
+            for _ in range(max(args.warmup, 3)):
+                per_cluster()
+            loop_ms = _timed_events(per_cluster, args.steps, flush, stream, torch)
+        st = ctx.sync_status(stream)
+    g, l = statistics.mean(graph_ms), statistics.mean(loop_ms)
+    print(json.dumps({
+        "metric": "regular-force interactions/s, 64 independent clusters, one persistent launch in a CUDA graph",
+        "value": inter / (g / 1e3), "unit": "interactions/s", "n_gpus": 1, "steps": args.steps,
+        "warmup": max(args.warmup, 3), "ms_per_step": g, "higher_is_better": True, "dtype": "f32",
+        "data": "synthetic", "status": st,
+        "config": {"workload": "64 equal-mass Plummer clusters, N log-uniform in [1024, 32768], n_act "
+                               "log-uniform in [8, N], ~64 neighbours, cap 256, seed 4",
+                   "mode": args.mode, "N_total": int(sum(w.n for w in ws)),
+                   "n_act_total": int(sum(w.n_act for w in ws)), "interactions_per_step": inter,
+                   "l2": "flushed between timed steps"},
+        "per_cluster_launches": {"value": inter / (l / 1e3), "ms_per_step": l,
+                                 "launches_per_step": 1 + len(ws)},
+        "graph_launches_per_step": plan_launches, "speedup_vs_per_cluster": l / g,
+    }), flush=True)
+
+
+def run_offset_pairs(args):
+    """N = 262144 cluster offset to |x_c| = 1e3 with 10% of the particles in hard
+    pairs: FP32, two-float (default and exact pair form) and FP64 forms, their
+    throughput and their errors against the oracle on sampled rows."""
+    import numpy as np
+    import torch
+
+    import oracle
+    from paper_1205_1222_gb300 import build, inputs
+    build.build()
+    torch.cuda.set_device(0)
+    full = inputs.cached(inputs.config5)
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
+    x, v = oracle.predict(full.x0, full.v0, full.a0, full.adot0, full.t0, full.t)
+    res = {}
+    for n_act in (4096, full.n):
+        w = full if n_act == full.n else inputs.subset(full, n_act, 5)
+        rows = np.arange(w.n_act) if w.n_act <= 4096 else \
+            np.sort(np.random.default_rng(5).choice(w.n_act, 4096, replace=False))
+        o = oracle.regular(x, v, w.m, w.act[rows], w.h[rows], cap=w.cap)
+        for label, mode, cfg in (("fp32", "fp32", ""), ("mixed", "mixed", ""), ("mixed_exact_pair", "mixed", "16,2,512,2"),
+                                 ("fp64", "fp64", "")):
+            r = Runner(w, mode, 0, cfg)
+            if not cfg and mode != "fp64" and not args.no_tune:
+                r.autotune()
+            r.predict(); r.force()
+            k = 1 if mode == "fp64" and n_act == full.n else max(2, min(args.steps, 5))
+            ms = statistics.mean(r.timed(k, flush)[1])
+            g = r.outputs()
+            r.close()
+            res[f"{label}@{n_act}"] = {"value": w.n * w.n_act / (ms / 1e3), "kernel_ms": ms, "tiling": r.cfg,
+                                       "accuracy": accuracy(g, o, rows, w.cap)}
+    print(json.dumps({
+        "metric": "regular-force interactions/s and errors vs the FP64 oracle, offset cluster with hard pairs",
+        "unit": "interactions/s", "n_gpus": 1, "dtype": "f32/f64", "data": "synthetic",
+        "config": {"workload": "equal-mass Plummer, N=262144, centre at |x|=1e3, 10% in hard pairs "
+                               "(separations 1e-5..1e-2), ~128 neighbours, cap 256, seed 5",
+                   "n_act": [4096, full.n], "oracle_rows": "all 4096 / a seeded 4096-row sample"},
+        "forms": res,
+    }), flush=True)
+
+
+def run_velocity(args):
+    """The headline workload with the velocity criterion min(|R|, |R + dtr V|) < h
+    (dtr per particle from the regular steps 2^-6 .. 2^-9) against the plain
+    criterion, two-float form, with errors on sampled rows."""
+    import numpy as np
+    import torch
+
+    import oracle
+    from paper_1205_1222_gb300 import build, inputs
+    build.build()
+    torch.cuda.set_device(0)
+    w = inputs.cached(inputs.cluster, 131072, 3, 100, 256, "hierarchy", 2.0**-10, "kroupa", 0.0, 0.0, None, None,
+                      (2.0**-6, 2.0**-7, 2.0**-8, 2.0**-9), key="kroupa_plummer_n131072_dtr")
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
+    rows = np.sort(np.random.default_rng(7).choice(w.n_act, 2048, replace=False))
+    x, v = oracle.predict(w.x0, w.v0, w.a0, w.adot0, w.t0, w.t)
+    res = {}
+    for crit in ("plain", "velocity"):
+        o = oracle.regular(x, v, w.m, w.act[rows], w.h[rows], dtr=w.dtr[rows] if crit == "velocity" else None,
+                           cap=w.cap)
+        r = Runner(w, args.mode, 0, "")
+        r.use_dtr = crit == "velocity"
+        if not args.no_tune:
+            r.autotune()
+        r.predict(); r.force()
+        ms = statistics.mean(r.timed(max(2, min(args.steps, 5)), flush)[1])
+        g = r.outputs()
+        r.close()
+        res[crit] = {"value": w.n * w.n_act / (ms / 1e3), "kernel_ms": ms, "tiling": r.cfg,
+                     "accuracy": accuracy(g, o, rows, w.cap)}
+    print(json.dumps({
+        "metric": "regular-force interactions/s with the velocity neighbour criterion vs the plain one",
+        "unit": "interactions/s", "n_gpus": 1, "dtype": "f32", "data": "synthetic", "mode": args.mode,
+        "config": {"workload": "Kroupa-IMF Plummer sphere N=131072, all active, ~100 neighbours, cap 256, seed 3, "
+                               "dtr per particle in {2^-6..2^-9}", "oracle_rows": 2048},
+        "criteria": res, "cost_of_velocity_criterion": res["velocity"]["kernel_ms"] / res["plain"]["kernel_ms"],
+    }), flush=True)
+
+
 def main():
     args = parse_args()
     if args.impl == "reference":
         run_reference(args)
+    elif args.workload == "batched64":
+        run_batched(args)
+    elif args.workload == "offset-pairs":
+        run_offset_pairs(args)
+    elif args.workload == "velocity":
+        run_velocity(args)
     else:
         run_ours(args)
 
