@@ -289,6 +289,13 @@ __device__ __forceinline__ void frame_tile(unsigned char *st, const Frame2 &fr, 
     }
 }
 
+// Neighbour-list state of one i-particle of a warp (shared memory).
+struct __align__(16) ListRec {
+    int32_t *row;   // its list row (final, or its j-split's partial row)
+    int32_t gi;     // its own index in the j-range (-1: no particle), skipped as self
+    int32_t cnt;    // neighbours found so far
+};
+
 // Marker for the kernels without frames.
 struct NoFrame {};
 
@@ -306,9 +313,9 @@ struct PairLayout {
     // float-float totals: one (hi, lo) float2 per (warp, i, component, lane)
     static constexpr int TOT = STAGES + NST * STAGE;
     __host__ __device__ static constexpr int tot_bytes(bool pot) { return W * I * (pot ? 7 : 6) * 32 * 8; }
-    __host__ __device__ static constexpr int cnt(bool pot) { return TOT + tot_bytes(pot); }
-    __host__ __device__ static constexpr int gi(bool pot) { return cnt(pot) + W * I * 4; }
-    __host__ __device__ static constexpr int desc(bool pot) { return gi(pot) + W * I * 4; }
+    // per (warp, i): the list row, the i's own j-index and the count so far
+    __host__ __device__ static constexpr int rec(bool pot) { return TOT + tot_bytes(pot); }
+    __host__ __device__ static constexpr int desc(bool pot) { return rec(pot) + W * I * 16; }
     __host__ __device__ static constexpr int bytes(bool pot)
     {
         return desc(pot) + W * static_cast<int>(sizeof(ClusterDesc));
@@ -384,8 +391,7 @@ __global__ void __launch_bounds__(W * 32, MINB) regf3_kernel(const RegfParams p)
     int *claim = rel + NST;                                       // warps that reached the stage
     unsigned char *stages = smem + L::STAGES;
     float2 *s_tot = reinterpret_cast<float2 *>(smem + L::TOT);
-    int *s_cnt = reinterpret_cast<int *>(smem + L::cnt(POT));
-    int *s_gi = reinterpret_cast<int *>(smem + L::gi(POT));
+    ListRec *s_rec = reinterpret_cast<ListRec *>(smem + L::rec(POT));
     ClusterDesc *s_d = reinterpret_cast<ClusterDesc *>(smem + L::desc(POT));
 
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
@@ -412,8 +418,7 @@ __global__ void __launch_bounds__(W * 32, MINB) regf3_kernel(const RegfParams p)
     uint32_t g = 0;
     bool aborted = false;
     float2 *mytot = s_tot + warp * I * NC * 32 + lane;   // + (i * NC + comp) * 32: (hi, lo)
-    int *mycnt = s_cnt + warp * I;
-    int *mygi = s_gi + warp * I;
+    ListRec *myrec = s_rec + warp * I;
     ClusterDesc &d = s_d[warp];
 
     // One work item (i-block ib, j-split sp) with the pair arithmetic of form P.
@@ -448,7 +453,15 @@ __global__ void __launch_bounds__(W * 32, MINB) regf3_kernel(const RegfParams p)
                 }
             }
             oidx[k] = gi >= 0 ? idx : -1;
-            if (lane == 0) { mygi[k] = gi; mycnt[k] = 0; }
+            if (lane == 0) {
+                ListRec r;
+                r.row = gi < 0 ? nullptr
+                               : d.n_split == 1 ? d.list + static_cast<int64_t>(idx) * d.cap
+                                                : d.plist + (static_cast<int64_t>(sp) * d.n_act + idx) * d.cap;
+                r.gi = gi;
+                r.cnt = 0;
+                myrec[k] = r;
+            }
             P::set_i(ipart[k], p.soa, slot, h2v, dtv, fr);
             for (int c = 0; c < 3; c++) acc[k].f[c] = acc[k].j[c] = 0ull;
             acc[k].p = 0ull;
@@ -535,25 +548,21 @@ __global__ void __launch_bounds__(W * 32, MINB) regf3_kernel(const RegfParams p)
                     const int pl = unit * 32 + lane;
                     const bool fa = (bits[q] >> (2 * unit)) & 1u, fb = (bits[q] >> (2 * unit + 1)) & 1u;
                     const int ja = jt0 + 2 * pl;
-                    const int gq = mygi[q];
-                    const bool xa = fa && ja != gq, xb = fb && ja + 1 != gq;
+                    const int2 gc = *reinterpret_cast<const int2 *>(&myrec[q].gi);   // (gi, cnt)
+                    const bool xa = fa && ja != gc.x, xb = fb && ja + 1 != gc.x;
                     const unsigned ma = __ballot_sync(0xffffffffu, xa);
                     const unsigned mb = __ballot_sync(0xffffffffu, xb);
-                    const int c0 = mycnt[q];
                     const unsigned lt = lanemask_lt();
-                    const int pa = c0 + __popc(ma & lt) + __popc(mb & lt);
+                    const int pa = gc.y + __popc(ma & lt) + __popc(mb & lt);
                     const int pb = pa + (xa ? 1 : 0);
-                    if ((xa && pa < d.cap) || (xb && pb < d.cap)) {
-                        const int64_t idx = oidx[q];
-                        int32_t *row = d.n_split == 1
-                                           ? d.list + idx * d.cap
-                                           : d.plist + (static_cast<int64_t>(sp) * d.n_act + idx) * d.cap;
-                        if (xa && pa < d.cap) row[pa] = ja;
-                        if (xb && pb < d.cap) row[pb] = ja + 1;
+                    const int cap = d.cap;
+                    if ((xa && pa < cap) || (xb && pb < cap)) {
+                        int32_t *row = myrec[q].row;
+                        if (xa && pa < cap) row[pa] = ja;
+                        if (xb && pb < cap) row[pb] = ja + 1;
                     }
-                    __syncwarp();
-                    if (lane == 0) mycnt[q] = c0 + __popc(ma) + __popc(mb);
-                    __syncwarp();
+                    // every lane stores the same new count and later reads its own store
+                    myrec[q].cnt = gc.y + __popc(ma) + __popc(mb);
                 }
             }
 
@@ -599,7 +608,7 @@ __global__ void __launch_bounds__(W * 32, MINB) regf3_kernel(const RegfParams p)
             }
             const int64_t i = oidx[q];
             if (lane == 0 && i >= 0) {
-                const int cnt = mycnt[q];
+                const int cnt = myrec[q].cnt;
                 if (d.n_split == 1) {
                     for (int c = 0; c < 3; c++) { d.F[3 * i + c] = out[c]; d.J[3 * i + c] = out[3 + c]; }
                     if (POT && d.pot) d.pot[i] = out[6];
