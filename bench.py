@@ -55,11 +55,12 @@ def parse_args():
     ap.add_argument("--config", default="", help="kernel tiling warps,ipw,jtile,packed[,split] "
                                                  "(default: the autotuner's choice)")
     ap.add_argument("--no-tune", action="store_true", help="skip the autotuner (library default tiling)")
-    ap.add_argument("--workload", default="headline", choices=["headline", "batched64", "offset-pairs", "velocity"],
+    ap.add_argument("--workload", default="headline", choices=["headline", "batched64", "offset-pairs", "velocity", "irregular"],
                     help="headline: the benchmark line; batched64: 64 independent clusters, one persistent "
                          "launch in a CUDA graph vs one launch per cluster; offset-pairs: N=262144 offset "
                          "cluster with 10%% hard pairs, FP32 vs two-float vs FP64 with errors; velocity: the "
-                         "headline workload with the velocity neighbour criterion")
+                         "headline workload with the velocity neighbour criterion; irregular: the irregular "
+                         "force over the lists of the headline workload")
     ap.add_argument("--n", type=int, default=131072,
                     help="j-particles (131072 = the benchmark workload; smaller N builds the same kind of "
                          "cluster, used for profiling captures)")
@@ -712,6 +713,58 @@ def run_velocity(args):
     }), flush=True)
 
 
+def run_irregular(args):
+    """The irregular force (Sec. 3.3 step (iv)) over the neighbour lists of the
+    headline workload, all three forms, against the oracle on sampled rows; the
+    work is a gather of each neighbour's predicted record."""
+    import numpy as np
+    import torch
+
+    import oracle
+    from paper_1205_1222_gb300 import build
+    build.build()
+    torch.cuda.set_device(0)
+    w = workload(args.n_act, args.n)
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
+    rows = np.sort(np.random.default_rng(11).choice(w.n_act, 2048, replace=False))
+    x, v = oracle.predict(w.x0, w.v0, w.a0, w.adot0, w.t0, w.t)
+    oF, oJ = oracle.irregular(x, v, w.m, w.act[rows], w.h[rows])
+    res = {}
+    bytes_per = {"fp64": 64, "mixed": 64, "fp32": 32}
+    for mode in ("fp64", "mixed", "fp32"):
+        r = Runner(w, mode, 0, "")
+        r.predict(); r.force()
+        torch.cuda.synchronize()
+        nnb = r.out["nnb"]
+        pairs = int(nnb.sum().item())
+        stream = r.stream
+        res_out = {}
+
+        def irr():
+            res_out["o"] = r.ctx.irregular_force(r.d["act"], nnb, r.out["list"], w.n, w.cap, mode=mode, stream=stream)
+        for _ in range(3):
+            irr()
+        ms = statistics.mean(_timed_events(irr, max(3, min(args.steps, 10)), flush, stream, torch))
+        st = r.ctx.sync_status()
+        g = {k: v.cpu().numpy() for k, v in res_out["o"].items() if v is not None}
+        r.close()
+
+        def rel(a, b):
+            nb = np.linalg.norm(b, axis=1)
+            return np.linalg.norm(a - b, axis=1) / np.where(nb > 0, nb, 1.0)
+        algo = pairs * (bytes_per[mode] + 4) + w.n_act * (2 * bytes_per[mode] + 8 + 48)
+        res[mode] = {"value": pairs / (ms / 1e3), "kernel_ms": ms, "status": st, "neighbour_pairs": pairs,
+                     "algorithmic_GBps": algo / (ms / 1e3) / 1e9,
+                     "F_max": float(rel(g["F"][rows], oF).max()), "J_max": float(rel(g["J"][rows], oJ).max())}
+    print(json.dumps({
+        "metric": "irregular-force neighbour interactions/s over the regular-force lists",
+        "unit": "interactions/s", "n_gpus": 1, "dtype": "f64/f32", "data": "synthetic",
+        "config": {"workload": describe(w, "all")["workload"], "oracle_rows": 2048,
+                   "bytes": "per neighbour: its predicted record (64 B FP64 / two-float, 32 B FP32) + 4 B index"},
+        "forms": res,
+    }), flush=True)
+
+
 def main():
     args = parse_args()
     if args.impl == "reference":
@@ -722,6 +775,8 @@ def main():
         run_offset_pairs(args)
     elif args.workload == "velocity":
         run_velocity(args)
+    elif args.workload == "irregular":
+        run_irregular(args)
     else:
         run_ours(args)
 

@@ -248,6 +248,22 @@ int nb_time_regular_force(nb_ctx *ctx, const nb_kcfg *cfg, int64_t j_begin, int6
                           double *pot, int32_t *nnb, int32_t *list, uint8_t *ovf, int reps,
                           nb_stream_t stream, float *ms);
 
+/* Irregular force (Sec. 3.3 step (iv); the paper computes it on the host):
+ * for each active particle i, F_i, J_i (and, if pot != NULL, the potential
+ * sum m_j/|R|) over the neighbour list row i, i.e. the first min(nnb[i], cap)
+ * entries of list[i*cap ...], with R = x_j - x_i, V = v_j - v_i from the
+ * predicted j-set in the form of `mode` (which must have been predicted).
+ * act, nnb and list index the j-range [j_begin, j_begin + n_j) as for
+ * nb_regular_force, whose outputs they usually are; with nnb[i] <= cap the sum
+ * is the irregular force of the paper, and F_reg + F_irr is the full direct sum.
+ * Outputs are FP64 (FP64 accumulation in every mode).  Device pointers,
+ * asynchronous on `stream`; an active index outside the range, a negative
+ * count, or a list entry outside the range or equal to i itself is skipped and
+ * reported as NB_ERR_DEVICE_INPUT by nb_sync_status. */
+int nb_irregular_force(nb_ctx *ctx, int64_t j_begin, int64_t n_j, int32_t n_act, const int32_t *act,
+                       const int32_t *nnb, const int32_t *list, int32_t cap, int mode, double *F,
+                       double *J, double *pot, nb_stream_t stream);
+
 /* Autotuner.  A call's size class is (mode, flags, floor(log2 n_act),
  * floor(log2 n_j)), flags = 1 with a velocity criterion (dtr != NULL) | 2 with
  * a potential output.  nb_autotune times, on the caller's own call (the same

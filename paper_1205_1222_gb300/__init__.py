@@ -74,6 +74,18 @@ class Context:
                             out["J"], out["pot"], out["nnb"], out["list"], out["ovf"], stream)
         return out
 
+    def irregular_force(self, act, nnb, lst, n_j, cap, mode="mixed", j_begin=0, pot=False, stream=None):
+        """Irregular force and jerk over the neighbour lists (FP64 outputs)."""
+        import torch
+        n_act = int(act.shape[0])
+        dev = torch.device("cuda", self.device)
+        out = {"F": torch.empty((n_act, 3), dtype=torch.float64, device=dev),
+               "J": torch.empty((n_act, 3), dtype=torch.float64, device=dev),
+               "pot": torch.empty((n_act,), dtype=torch.float64, device=dev) if pot else None}
+        _b.nb_irregular_force(self.h, j_begin, n_j, n_act, act, nnb, lst, cap, mode_id(mode), out["F"], out["J"],
+                              out["pot"], stream)
+        return out
+
     def sync_status(self, stream=None) -> int:
         return _b.nb_sync_status(self.h, stream)
 

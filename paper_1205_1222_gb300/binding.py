@@ -37,7 +37,7 @@ EXPORTS = [
     "nb_strerror", "nb_last_error", "nb_num_kernel_configs", "nb_get_kernel_config",
     "nb_set_kernel_config", "nb_get_active_config", "nb_time_regular_force", "nb_last_launches",
     "nb_sm_count", "nb_debug_set_wait", "nb_regular_force_noalloc", "nb_debug_frame_stats",
-    "nb_autotune", "nb_num_tuned", "nb_get_tuned", "nb_set_tuned",
+    "nb_autotune", "nb_num_tuned", "nb_get_tuned", "nb_set_tuned", "nb_irregular_force",
 ]
 
 
@@ -116,6 +116,7 @@ def library():
         "nb_autotune": ([P, i64, i64, i32, P, P, P, i32, cint, P, P, P, P, P, P, cint, P,
                          ctypes.POINTER(nb_kcfg), ctypes.POINTER(ctypes.c_float)], cint),
         "nb_num_tuned": ([P], cint),
+        "nb_irregular_force": ([P, i64, i64, i32, P, P, P, i32, cint, P, P, P, P], cint),
         "nb_get_tuned": ([P, cint, ctypes.POINTER(nb_tuned)], cint),
         "nb_set_tuned": ([P, ctypes.POINTER(nb_tuned)], cint),
     }
@@ -193,6 +194,12 @@ def nb_regular_force(ctx, j_begin, n_j, n_act, act, h, dtr, cap, mode, F, J, pot
     _check(ctx, library().nb_regular_force(ctx, int(j_begin), int(n_j), int(n_act), _p(act), _p(h), _p(dtr),
                                            int(cap), int(mode), _p(F), _p(J), _p(pot), _p(nnb), _p(lst),
                                            _p(ovf), _stream(stream)), "nb_regular_force")
+
+
+def nb_irregular_force(ctx, j_begin, n_j, n_act, act, nnb, lst, cap, mode, F, J, pot=None, stream=None):
+    _check(ctx, library().nb_irregular_force(ctx, int(j_begin), int(n_j), int(n_act), _p(act), _p(nnb), _p(lst),
+                                             int(cap), int(mode), _p(F), _p(J), _p(pot), _stream(stream)),
+           "nb_irregular_force")
 
 
 def nb_regular_force_noalloc(ctx, j_begin, n_j, n_act, act, h, dtr, cap, mode, F, J, pot, nnb, lst, ovf,

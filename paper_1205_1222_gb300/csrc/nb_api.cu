@@ -16,6 +16,7 @@
 #include <cuda_runtime.h>
 
 #include "nb_aux.cuh"
+#include "nb_irr.cuh"
 #include "nb_sort.cuh"
 #include "nbreg.h"
 
@@ -703,6 +704,45 @@ int nb_time_regular_force(nb_ctx *ctx, const nb_kcfg *cfg, int64_t j_begin, int6
     if (rc != NB_OK) return rc;
     if (e != cudaSuccess) return cuda_fail(ctx, e, "timing events");
     *ms = t / reps;
+    return NB_OK;
+}
+
+// ------------------------------------------------------------ irregular force
+
+int nb_irregular_force(nb_ctx *ctx, int64_t j_begin, int64_t n_j, int32_t n_act, const int32_t *act,
+                       const int32_t *nnb, const int32_t *list, int32_t cap, int mode, double *F,
+                       double *J, double *pot, nb_stream_t stream)
+{
+    if (!ctx) return NB_ERR_ARG;
+    if (mode < NB_FP64 || mode > NB_FP32) { ctx->err = "bad mode"; return NB_ERR_ARG; }
+    if (j_begin < 0 || n_j < 0 || j_begin + n_j > ctx->n_max || n_j > INT32_MAX) {
+        ctx->err = "j-range outside the context";
+        return NB_ERR_ARG;
+    }
+    if (n_act < 0 || cap < 0) { ctx->err = "negative n_act or cap"; return NB_ERR_ARG; }
+    if (n_act == 0) return NB_OK;
+    if (n_j == 0) { ctx->err = "active particles with an empty j-range"; return NB_ERR_ARG; }
+    if (!act || !nnb || !F || !J || (cap > 0 && !list)) { ctx->err = "NULL array"; return NB_ERR_ARG; }
+    if (!(ctx->forms_valid & mode_forms(mode))) {
+        ctx->err = "the requested form has not been predicted";
+        return NB_ERR_STATE;
+    }
+    DeviceGuard guard(ctx->device);
+    nb::IrrParams p{};
+    p.j_begin = j_begin;
+    p.n_j = static_cast<int32_t>(n_j);
+    p.n_act = n_act;
+    p.cap = cap;
+    p.act = act;
+    p.nnb = nnb;
+    p.list = list;
+    p.js = jset(ctx, mode);
+    p.F = F;
+    p.J = J;
+    p.pot = pot;
+    p.status = ctx->d_status;
+    NB_CUDA(ctx, nb::launch_irregular(p, mode, ctx->sm_count, static_cast<cudaStream_t>(stream)));
+    ctx->last_launches = 1;
     return NB_OK;
 }
 

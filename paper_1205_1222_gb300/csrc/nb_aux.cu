@@ -50,8 +50,9 @@ __global__ void predict_kernel(const PredParams p)
             vh[k] = __double2float_rn(v[k]);
             vl[k] = __double2float_rn(v[k] - static_cast<double>(vh[k]));
         }
-        p.mx_hi[s] = make_float4(xh[0], xh[1], xh[2], __double2float_rn(m));
-        p.mx_lo[s] = make_float4(xl[0], xl[1], xl[2], 0.f);
+        const float mh = __double2float_rn(m);
+        p.mx_hi[s] = make_float4(xh[0], xh[1], xh[2], mh);
+        p.mx_lo[s] = make_float4(xl[0], xl[1], xl[2], __double2float_rn(m - static_cast<double>(mh)));
         p.mv_hi[s] = make_float4(vh[0], vh[1], vh[2], 0.f);
         p.mv_lo[s] = make_float4(vl[0], vl[1], vl[2], 0.f);
     }

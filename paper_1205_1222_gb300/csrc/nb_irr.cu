@@ -1,0 +1,159 @@
+// Irregular force and jerk over the neighbour lists (Sec. 3.3 step (iv),
+// Sec. 3.5): for each active particle i, the Newtonian force
+//   F_i = sum_{j in L_i} m_j R / |R|^3,  J_i = sum_{j in L_i} m_j (V / |R|^3 - 3 (R.V) R / |R|^5)
+// (and optionally the potential sum m_j / |R|) over the entries of its list,
+// R = x_j - x_i, V = v_j - v_i, from the context's predicted j-set.  The paper
+// evaluates this sum on the host with SSE/AVX; here it is one warp per active
+// particle, lanes over the list entries, FP64 accumulation and a warp
+// reduction.  The work is a gather of ~100 scattered j per i: bound by L2 / HBM
+// access, not by arithmetic.
+//
+// Forms: FP64 throughout; two-float coordinates and mass (Sec. 3.5 keeps
+// two-float coordinates for this sum, since close pairs live here) differenced
+// exactly in FP64, with FP64 terms (the few neighbours' forces cancel, so an
+// FP32 mass alone cost ~6e-7 with Kroupa masses): a pair at 1e-5 separation 1e3 from the origin keeps the ~48 bits of
+// the two-float coordinates, where FP32 terms lost a further ~1e-6; plain FP32
+// differences and terms.
+#include <cfloat>
+
+#include "nb_irr.cuh"
+
+namespace nb {
+
+namespace {
+
+struct IrrTerm {
+    double f[3], j[3], p;
+};
+
+__device__ __forceinline__ void add_term(IrrTerm &a, double m, double rinv, const double dx[3], const double dv[3])
+{
+    const double rinv2 = rinv * rinv;
+    const double mr = m * rinv;
+    const double mr3 = mr * rinv2;
+    const double al = 3.0 * (dx[0] * dv[0] + dx[1] * dv[1] + dx[2] * dv[2]) * rinv2;
+    for (int c = 0; c < 3; c++) {
+        a.f[c] += mr3 * dx[c];
+        a.j[c] += mr3 * (dv[c] - al * dx[c]);
+    }
+    a.p += mr;
+}
+
+__device__ __forceinline__ void add_term_f(IrrTerm &a, float m, const float dx[3], const float dv[3])
+{
+    const float r2 = dx[0] * dx[0] + dx[1] * dx[1] + dx[2] * dx[2];
+    const float rinv = rsqrtf(r2);
+    const float rinv2 = rinv * rinv;
+    const float mr = m * rinv;
+    const float mr3 = mr * rinv2;
+    const float al = 3.f * (dx[0] * dv[0] + dx[1] * dv[1] + dx[2] * dv[2]) * rinv2;
+    for (int c = 0; c < 3; c++) {
+        a.f[c] += static_cast<double>(mr3 * dx[c]);
+        a.j[c] += static_cast<double>(mr3 * (dv[c] - al * dx[c]));
+    }
+    a.p += static_cast<double>(mr);
+}
+
+template <int MODE, bool POT>
+__global__ void __launch_bounds__(256) irr_kernel(const IrrParams p)
+{
+    const int lane = threadIdx.x & 31;
+    const int64_t warps = static_cast<int64_t>(gridDim.x) * (blockDim.x >> 5);
+    for (int64_t i = static_cast<int64_t>(blockIdx.x) * (blockDim.x >> 5) + (threadIdx.x >> 5); i < p.n_act;
+         i += warps) {
+        const int a = p.act[i];
+        const int nn = p.nnb[i];
+        if (a < 0 || a >= p.n_j || nn < 0) {
+            if (lane == 0) atomicOr(p.status, DEV_BAD_INPUT);
+            continue;
+        }
+        const int k = min(nn, p.cap);
+        const int64_t si = p.j_begin + a;
+        const int32_t *row = p.list + i * static_cast<int64_t>(p.cap);
+        IrrTerm t{};
+        if (MODE == 0) {   // FP64
+            const double4_32a xi = reinterpret_cast<const double4_32a *>(p.js.s[0])[si];
+            const double4_32a vi = reinterpret_cast<const double4_32a *>(p.js.s[1])[si];
+            for (int e = lane; e < k; e += 32) {
+                const int j = row[e];
+                if (j < 0 || j >= p.n_j || j == a) { atomicOr(p.status, DEV_BAD_INPUT); continue; }
+                const double4_32a xj = reinterpret_cast<const double4_32a *>(p.js.s[0])[p.j_begin + j];
+                const double4_32a vj = reinterpret_cast<const double4_32a *>(p.js.s[1])[p.j_begin + j];
+                const double dx[3] = {xj.x - xi.x, xj.y - xi.y, xj.z - xi.z};
+                const double dv[3] = {vj.x - vi.x, vj.y - vi.y, vj.z - vi.z};
+                const double r2 = dx[0] * dx[0] + dx[1] * dx[1] + dx[2] * dx[2];
+                add_term(t, xj.w, 1.0 / sqrt(r2), dx, dv);
+            }
+        } else if (MODE == 1) {   // two-float coordinates, exact FP64 differences, FP64 terms
+            const float4 *xh = reinterpret_cast<const float4 *>(p.js.s[0]);
+            const float4 *xl = reinterpret_cast<const float4 *>(p.js.s[1]);
+            const float4 *vh = reinterpret_cast<const float4 *>(p.js.s[2]);
+            const float4 *vl = reinterpret_cast<const float4 *>(p.js.s[3]);
+            const float4 ih = xh[si], il = xl[si], jh = vh[si], jl = vl[si];
+            for (int e = lane; e < k; e += 32) {
+                const int j = row[e];
+                if (j < 0 || j >= p.n_j || j == a) { atomicOr(p.status, DEV_BAD_INPUT); continue; }
+                const int64_t sj = p.j_begin + j;
+                const float4 ah = xh[sj], al = xl[sj], bh = vh[sj], bl = vl[sj];
+                // differences of FP32 values are exact in FP64, so these are the
+                // two-float differences without further rounding
+                auto d2 = [](float a, float b, float c, float e) {
+                    return (static_cast<double>(a) - b) + (static_cast<double>(c) - e);
+                };
+                const double dx[3] = {d2(ah.x, ih.x, al.x, il.x), d2(ah.y, ih.y, al.y, il.y), d2(ah.z, ih.z, al.z, il.z)};
+                const double dv[3] = {d2(bh.x, jh.x, bl.x, jl.x), d2(bh.y, jh.y, bl.y, jl.y), d2(bh.z, jh.z, bl.z, jl.z)};
+                const double r2 = dx[0] * dx[0] + dx[1] * dx[1] + dx[2] * dx[2];
+                add_term(t, static_cast<double>(ah.w) + al.w, 1.0 / sqrt(r2), dx, dv);   // two-float mass
+            }
+        } else {   // FP32
+            const float4 *x = reinterpret_cast<const float4 *>(p.js.s[0]);
+            const float4 *v = reinterpret_cast<const float4 *>(p.js.s[1]);
+            const float4 xi = x[si], vi = v[si];
+            for (int e = lane; e < k; e += 32) {
+                const int j = row[e];
+                if (j < 0 || j >= p.n_j || j == a) { atomicOr(p.status, DEV_BAD_INPUT); continue; }
+                const int64_t sj = p.j_begin + j;
+                const float4 xj = x[sj], vj = v[sj];
+                const float dx[3] = {xj.x - xi.x, xj.y - xi.y, xj.z - xi.z};
+                const float dv[3] = {vj.x - vi.x, vj.y - vi.y, vj.z - vi.z};
+                add_term_f(t, xj.w, dx, dv);
+            }
+        }
+        for (int o = 16; o > 0; o >>= 1) {
+            for (int c = 0; c < 3; c++) {
+                t.f[c] += __shfl_xor_sync(0xffffffffu, t.f[c], o);
+                t.j[c] += __shfl_xor_sync(0xffffffffu, t.j[c], o);
+            }
+            if (POT) t.p += __shfl_xor_sync(0xffffffffu, t.p, o);
+        }
+        if (lane == 0) {
+            for (int c = 0; c < 3; c++) {
+                p.F[3 * i + c] = t.f[c];
+                p.J[3 * i + c] = t.j[c];
+            }
+            if (POT) p.pot[i] = t.p;
+        }
+    }
+}
+
+template <int MODE>
+cudaError_t launch_mode(const IrrParams &p, int grid, cudaStream_t st)
+{
+    if (p.pot) irr_kernel<MODE, true><<<grid, 256, 0, st>>>(p);
+    else irr_kernel<MODE, false><<<grid, 256, 0, st>>>(p);
+    return cudaGetLastError();
+}
+
+}  // namespace
+
+cudaError_t launch_irregular(const IrrParams &p, int mode, int sm_count, cudaStream_t st)
+{
+    if (p.n_act <= 0) return cudaSuccess;
+    const int64_t want = (static_cast<int64_t>(p.n_act) + 7) / 8;   // 8 warps (active particles) per block
+    const int grid = static_cast<int>(std::min<int64_t>(want, static_cast<int64_t>(sm_count) * 8));
+    if (mode == 0) return launch_mode<0>(p, grid, st);
+    if (mode == 1) return launch_mode<1>(p, grid, st);
+    return launch_mode<2>(p, grid, st);
+}
+
+}  // namespace nb
