@@ -175,15 +175,19 @@ def kernel_source_hash():
     return h.hexdigest()[:16]
 
 
-def profiled_traffic():
+def profiled_traffic(tiling=None):
     """DRAM bytes per launch from the committed ncu summary, if it was taken
-    on the current kernel sources (else None)."""
+    on the current kernel sources and, when it names one, the same tiling
+    (else None)."""
     if not os.path.exists(PROFILE):
         return None
     text = open(PROFILE).read()
     mh = re.search(r"kernel_source_hash:\s*([0-9a-f]+)", text)
     mt = re.search(r"traffic_bytes_per_launch:\s*([0-9.eE+]+)", text)
+    mc = re.search(r"tiling:\s*([0-9, ]+)", text)
     if not mh or not mt or mh.group(1) != kernel_source_hash():
+        return None
+    if mc and tiling is not None and [int(x) for x in mc.group(1).split(",")] != list(tiling):
         return None
     return float(mt.group(1))
 
@@ -447,7 +451,7 @@ def run_ours(args):
     }
     line["roofline"] = {
         "bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
-        "traffic": profiled_traffic(),
+        "traffic": profiled_traffic(r.cfg),
         "kernel": "regular force + jerk + list kernel, one launch per step; tiling (warps, ipw, jtile, "
                   f"split, packed) = {r.cfg}",
         "kernel_ms": fms,
