@@ -599,7 +599,11 @@ def run_batched(args):
 
         with torch.cuda.stream(stream):
             predict()
-            plan = B.nb_plan_create(ctx.h, cl, mode)
+            pcfg = None
+            if args.config:
+                f = [int(x) for x in args.config.split(",")]
+                pcfg = B.nb_kcfg(f[0], f[1], f[2], f[4] if len(f) > 4 else 0, f[3])
+            plan = B.nb_plan_create(ctx.h, cl, mode, pcfg)
             try:
                 B.nb_plan_capture(plan, stream=stream, ctx=ctx.h)
                 for _ in range(max(args.warmup, 3)):
@@ -633,6 +637,7 @@ def run_batched(args):
         "per_cluster_launches": {"value": inter / (l / 1e3), "ms_per_step": l,
                                  "launches_per_step": 1 + len(ws)},
         "graph_launches_per_step": plan_launches, "speedup_vs_per_cluster": l / g,
+        "plan_tiling": args.config or "default",
     }), flush=True)
 
 

@@ -289,11 +289,12 @@ __device__ __forceinline__ void frame_tile(unsigned char *st, const Frame2 &fr, 
     }
 }
 
-// Neighbour-list state of one i-particle of a warp (shared memory).
+// List target of one i-particle of a warp (shared memory; the running count
+// stays in a register).
 struct __align__(16) ListRec {
     int32_t *row;   // its list row (final, or its j-split's partial row)
     int32_t gi;     // its own index in the j-range (-1: no particle), skipped as self
-    int32_t cnt;    // neighbours found so far
+    int32_t pad;
 };
 
 // Marker for the kernels without frames.
@@ -313,7 +314,7 @@ struct PairLayout {
     // float-float totals: one (hi, lo) float2 per (warp, i, component, lane)
     static constexpr int TOT = STAGES + NST * STAGE;
     __host__ __device__ static constexpr int tot_bytes(bool pot) { return W * I * (pot ? 7 : 6) * 32 * 8; }
-    // per (warp, i): the list row, the i's own j-index and the count so far
+    // per (warp, i): the list row and the i's own j-index
     __host__ __device__ static constexpr int rec(bool pot) { return TOT + tot_bytes(pot); }
     __host__ __device__ static constexpr int desc(bool pot) { return rec(pot) + W * I * 16; }
     __host__ __device__ static constexpr int bytes(bool pot)
@@ -431,6 +432,7 @@ __global__ void __launch_bounds__(W * 32, MINB) regf3_kernel(const RegfParams p)
         IB ipart[I];
         Acc2 acc[I];
         int oidx[I];                 // output row of each i (its position in act)
+        int cnt[I];                  // neighbours found so far (the same in every lane)
         const int i0 = (ib * W + warp) * I;
 #pragma unroll
         for (int k = 0; k < I; k++) {
@@ -459,9 +461,10 @@ __global__ void __launch_bounds__(W * 32, MINB) regf3_kernel(const RegfParams p)
                                : d.n_split == 1 ? d.list + static_cast<int64_t>(idx) * d.cap
                                                 : d.plist + (static_cast<int64_t>(sp) * d.n_act + idx) * d.cap;
                 r.gi = gi;
-                r.cnt = 0;
+                r.pad = 0;
                 myrec[k] = r;
             }
+            cnt[k] = 0;
             P::set_i(ipart[k], p.soa, slot, h2v, dtv, fr);
             for (int c = 0; c < 3; c++) acc[k].f[c] = acc[k].j[c] = 0ull;
             acc[k].p = 0ull;
@@ -548,12 +551,12 @@ __global__ void __launch_bounds__(W * 32, MINB) regf3_kernel(const RegfParams p)
                     const int pl = unit * 32 + lane;
                     const bool fa = (bits[q] >> (2 * unit)) & 1u, fb = (bits[q] >> (2 * unit + 1)) & 1u;
                     const int ja = jt0 + 2 * pl;
-                    const int2 gc = *reinterpret_cast<const int2 *>(&myrec[q].gi);   // (gi, cnt)
-                    const bool xa = fa && ja != gc.x, xb = fb && ja + 1 != gc.x;
+                    const int gq = myrec[q].gi;
+                    const bool xa = fa && ja != gq, xb = fb && ja + 1 != gq;
                     const unsigned ma = __ballot_sync(0xffffffffu, xa);
                     const unsigned mb = __ballot_sync(0xffffffffu, xb);
                     const unsigned lt = lanemask_lt();
-                    const int pa = gc.y + __popc(ma & lt) + __popc(mb & lt);
+                    const int pa = cnt[q] + __popc(ma & lt) + __popc(mb & lt);
                     const int pb = pa + (xa ? 1 : 0);
                     const int cap = d.cap;
                     if ((xa && pa < cap) || (xb && pb < cap)) {
@@ -561,8 +564,7 @@ __global__ void __launch_bounds__(W * 32, MINB) regf3_kernel(const RegfParams p)
                         if (xa && pa < cap) row[pa] = ja;
                         if (xb && pb < cap) row[pb] = ja + 1;
                     }
-                    // every lane stores the same new count and later reads its own store
-                    myrec[q].cnt = gc.y + __popc(ma) + __popc(mb);
+                    cnt[q] += __popc(ma) + __popc(mb);
                 }
             }
 
@@ -608,16 +610,16 @@ __global__ void __launch_bounds__(W * 32, MINB) regf3_kernel(const RegfParams p)
             }
             const int64_t i = oidx[q];
             if (lane == 0 && i >= 0) {
-                const int cnt = myrec[q].cnt;
+                const int nq = cnt[q];
                 if (d.n_split == 1) {
                     for (int c = 0; c < 3; c++) { d.F[3 * i + c] = out[c]; d.J[3 * i + c] = out[3 + c]; }
                     if (POT && d.pot) d.pot[i] = out[6];
-                    d.nnb[i] = cnt;
-                    d.ovf[i] = cnt > d.cap ? 1 : 0;
+                    d.nnb[i] = nq;
+                    d.ovf[i] = nq > d.cap ? 1 : 0;
                 } else {
                     double *o8 = d.pF + (static_cast<int64_t>(sp) * d.n_act + i) * 8;
                     for (int c = 0; c < 7; c++) o8[c] = c < NC ? out[c] : 0.0;
-                    d.pcnt[static_cast<int64_t>(sp) * d.n_act + i] = cnt;
+                    d.pcnt[static_cast<int64_t>(sp) * d.n_act + i] = nq;
                 }
             }
         }
