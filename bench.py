@@ -55,12 +55,13 @@ def parse_args():
     ap.add_argument("--config", default="", help="kernel tiling warps,ipw,jtile,packed[,split] "
                                                  "(default: the autotuner's choice)")
     ap.add_argument("--no-tune", action="store_true", help="skip the autotuner (library default tiling)")
-    ap.add_argument("--workload", default="headline", choices=["headline", "batched64", "offset-pairs", "velocity", "irregular"],
+    ap.add_argument("--workload", default="headline", choices=["headline", "batched64", "offset-pairs", "velocity", "irregular", "blockstep"],
                     help="headline: the benchmark line; batched64: 64 independent clusters, one persistent "
                          "launch in a CUDA graph vs one launch per cluster; offset-pairs: N=262144 offset "
                          "cluster with 10%% hard pairs, FP32 vs two-float vs FP64 with errors; velocity: the "
                          "headline workload with the velocity neighbour criterion; irregular: the irregular "
-                         "force over the lists of the headline workload")
+                         "force over the lists of the headline workload; blockstep: N=16384 with active "
+                         "subsets of 16..16384, two-float (autotuned) and FP64 forms")
     ap.add_argument("--n", type=int, default=131072,
                     help="j-particles (131072 = the benchmark workload; smaller N builds the same kind of "
                          "cluster, used for profiling captures)")
@@ -774,6 +775,48 @@ def run_irregular(args):
     }), flush=True)
 
 
+def run_blockstep(args):
+    """Block-step active subsets of the N = 16384 Plummer cluster (n_act = 16 ..
+    16384, steps 2^-3 .. 2^-12): prediction plus regular force per step for the
+    two-float form (autotuned per size class) and the FP64 form, with errors
+    against the oracle on every row."""
+    import numpy as np
+    import torch
+
+    import oracle
+    from paper_1205_1222_gb300 import build, inputs
+    build.build()
+    torch.cuda.set_device(0)
+    full = inputs.cached(inputs.config2)
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
+    x, v = oracle.predict(full.x0, full.v0, full.a0, full.adot0, full.t0, full.t)
+    res = []
+    for n_act in (16, 64, 256, 1024, 4096, 16384):
+        w = full if n_act == full.n else inputs.subset(full, n_act, 2)
+        o = oracle.regular(x, v, w.m, w.act, w.h, cap=w.cap)
+        row = {"n_act": n_act}
+        for mode in ("mixed", "fp64"):
+            r = Runner(w, mode, 0, "")
+            if mode == "mixed" and not args.no_tune:
+                r.autotune()
+            for _ in range(3):
+                r.predict(); r.force()
+            step_ms, force_ms = r.timed(max(3, min(args.steps, 10)), flush)
+            g = r.outputs()
+            r.close()
+            row[mode] = {"step_ms": statistics.mean(step_ms), "kernel_ms": statistics.mean(force_ms),
+                         "interactions_per_s": w.n * n_act / (statistics.mean(step_ms) / 1e3), "tiling": r.cfg,
+                         "accuracy": accuracy(g, o, np.arange(n_act), w.cap)}
+        res.append(row)
+    print(json.dumps({
+        "metric": "regular-force interactions/s per block step (prediction included) across active-set sizes",
+        "unit": "interactions/s", "n_gpus": 1, "dtype": "f32/f64", "data": "synthetic",
+        "config": {"workload": "equal-mass Plummer N=16384, seed 2, ~64 neighbours, cap 256, random active subsets",
+                   "l2": "flushed between timed steps"},
+        "sizes": res,
+    }), flush=True)
+
+
 def main():
     args = parse_args()
     if args.impl == "reference":
@@ -786,6 +829,8 @@ def main():
         run_velocity(args)
     elif args.workload == "irregular":
         run_irregular(args)
+    elif args.workload == "blockstep":
+        run_blockstep(args)
     else:
         run_ours(args)
 

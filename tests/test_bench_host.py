@@ -31,6 +31,15 @@ def test_profiled_traffic_requires_current_sources(tmp_path, monkeypatch):
     assert bench.profiled_traffic() is None
 
 
+def test_profiled_traffic_requires_the_same_tiling(tmp_path, monkeypatch):
+    p = tmp_path / "prof.md"
+    p.write_text(f"kernel_source_hash: {bench.kernel_source_hash()}\ntiling: 16, 2, 1536, 0, 5\n"
+                 "traffic_bytes_per_launch: 2.5e7\n")
+    monkeypatch.setattr(bench, "PROFILE", str(p))
+    assert bench.profiled_traffic((16, 2, 1536, 0, 5)) == 2.5e7
+    assert bench.profiled_traffic((16, 2, 1024, 0, 5)) is None
+
+
 def _free_port():
     s = socket.socket()
     s.bind(("127.0.0.1", 0))
