@@ -58,8 +58,11 @@ enum nb_status {
 /* Precision form of the pairwise arithmetic. */
 enum nb_mode {
     NB_FP64 = 0,  /* FP64 differences, FP64 pair terms, FP64 sums                   */
-    NB_MIXED = 1, /* two-float (hi+lo) position and velocity differences, FP32 pair  *
-                   * terms, float-float sums per lane, FP64 across lanes and splits  */
+    NB_MIXED = 1, /* two-float (hi+lo) position differences, FP32 pair terms,         *
+                   * float-float sums per lane, FP64 across lanes and splits; the   *
+                   * default tiling (packed = 5) differences FP32-rounded velocities,*
+                   * the exact pair tiling (packed = 2) and the scalar kernels     *
+                   * two-float velocities                                           */
     NB_FP32 = 2   /* plain FP32 differences and pair terms, same sums as NB_MIXED    */
 };
 
@@ -105,8 +108,9 @@ typedef struct nb_cluster {
 } nb_cluster;
 
 /* Open a context on CUDA device `device` for up to n_max j-particles
- * (~ GPUNB_OPEN, Appendix C).  Allocates the predicted j-set (160 bytes per
- * slot for all three forms) and the device status word.  *out is NULL on
+ * (~ GPUNB_OPEN, Appendix C).  Allocates the predicted j-set (248 bytes per
+ * slot for all three forms and their pair-interleaved copies) and the device
+ * status word.  *out is NULL on
  * failure.  Returns NB_ERR_ARG (n_max <= 0, bad device), NB_ERR_NOMEM or
  * NB_ERR_CUDA. */
 int nb_create(nb_ctx **out, int device, int64_t n_max);
@@ -123,7 +127,9 @@ void nb_destroy(nb_ctx *ctx);
  * x0, v0, a0, adot0: [n][3]; m, t0: [n]; all device pointers.
  * forms: NB_FORM_* bits of the stored copies to write (0 = all): FP64
  * (x,y,z,m)+(vx,vy,vz,0) as double4; MIXED hi/lo float pairs of position and
- * velocity with the mass in the hi-position w; FP32 float4 copies.
+ * velocity with the mass's hi and lo parts in the w of the position pair;
+ * FP32 float4 copies; the j-pair kernels' pair-interleaved copies of the
+ * MIXED and FP32 forms.
  * Errors: NB_ERR_ARG if offset < 0, n < 0, offset + n > n_max, a NULL array
  * with n > 0. */
 int nb_predict(nb_ctx *ctx, int64_t offset, int64_t n, const double *x0, const double *v0,
@@ -234,8 +240,10 @@ const char *nb_last_error(nb_ctx *ctx);
 /* Kernel configurations compiled for a mode (the autotuner's search space). */
 int nb_num_kernel_configs(int mode);
 int nb_get_kernel_config(int mode, int index, nb_kcfg *out);
-/* Select the configuration nb_regular_force uses for `mode` (NULL = built-in
- * default).  NB_ERR_UNSUPPORTED if no compiled kernel matches. */
+/* Select the configuration nb_regular_force uses for `mode` (NULL = back to
+ * the autotuned tiling of each call's size class, else the built-in default).
+ * NB_ERR_UNSUPPORTED if no compiled kernel matches.  nb_get_active_config
+ * reports the configuration set here, or the built-in default. */
 int nb_set_kernel_config(nb_ctx *ctx, int mode, const nb_kcfg *cfg);
 int nb_get_active_config(nb_ctx *ctx, int mode, nb_kcfg *out);
 
