@@ -130,19 +130,24 @@ __global__ void merge_kernel(const MergeParams p)
             const int t = __shfl_up_sync(0xffffffffu, incl, o);
             if (lane >= o) incl += t;
         }
-        const int base = running + incl - c;
-        unsigned todo = __ballot_sync(0xffffffffu, c > 0 && base < d.cap);
-        while (todo) {
-            const int src = __ffs(todo) - 1;
-            todo &= todo - 1;
-            const int sc = __shfl_sync(0xffffffffu, c, src);
-            const int sb = __shfl_sync(0xffffffffu, base, src);
-            const int ncopy = min(sc, d.cap - sb);
-            const int32_t *from = d.plist + (static_cast<int64_t>(s0 + src) * na + i) * d.cap;
-            int32_t *to = d.list + i * d.cap + sb;
-            for (int e = lane; e < ncopy; e += 32) to[e] = from[e];
+        // Copy the chunk's entries that still fit, one entry per lane per
+        // round: entry e of the chunk belongs to the last split whose
+        // exclusive prefix is <= e (found by a binary search over the lanes).
+        const int excl = incl - c;
+        const int total = __shfl_sync(0xffffffffu, incl, 31);
+        const int ncopy = max(0, min(total, d.cap - running));
+        int32_t *to = d.list + i * d.cap + running;
+        for (int r = 0; r < ncopy; r += 32) {
+            const int e = r + lane;
+            int src = 0;
+            for (int step = 16; step > 0; step >>= 1) {
+                const int ex = __shfl_sync(0xffffffffu, excl, src + step);
+                if (ex <= e) src += step;
+            }
+            const int off = e - __shfl_sync(0xffffffffu, excl, src);
+            if (e < ncopy) to[e] = d.plist[(static_cast<int64_t>(s0 + src) * na + i) * d.cap + off];
         }
-        running += __shfl_sync(0xffffffffu, incl, 31);
+        running += total;
     }
     for (int o = 16; o > 0; o >>= 1)
         for (int k = 0; k < 7; k++) sum[k] += __shfl_xor_sync(0xffffffffu, sum[k], o);
