@@ -82,7 +82,7 @@ __global__ void __launch_bounds__(256) irr_kernel(const IrrParams p)
                 const double dx[3] = {xj.x - xi.x, xj.y - xi.y, xj.z - xi.z};
                 const double dv[3] = {vj.x - vi.x, vj.y - vi.y, vj.z - vi.z};
                 const double r2 = dx[0] * dx[0] + dx[1] * dx[1] + dx[2] * dx[2];
-                add_term(t, xj.w, 1.0 / sqrt(r2), dx, dv);
+                add_term(t, xj.w, rsqrt(r2), dx, dv);
             }
         } else if (MODE == 1) {   // two-float coordinates, exact FP64 differences, FP64 terms
             const float4 *xh = reinterpret_cast<const float4 *>(p.js.s[0]);
@@ -103,7 +103,7 @@ __global__ void __launch_bounds__(256) irr_kernel(const IrrParams p)
                 const double dx[3] = {d2(ah.x, ih.x, al.x, il.x), d2(ah.y, ih.y, al.y, il.y), d2(ah.z, ih.z, al.z, il.z)};
                 const double dv[3] = {d2(bh.x, jh.x, bl.x, jl.x), d2(bh.y, jh.y, bl.y, jl.y), d2(bh.z, jh.z, bl.z, jl.z)};
                 const double r2 = dx[0] * dx[0] + dx[1] * dx[1] + dx[2] * dx[2];
-                add_term(t, static_cast<double>(ah.w) + al.w, 1.0 / sqrt(r2), dx, dv);   // two-float mass
+                add_term(t, static_cast<double>(ah.w) + al.w, rsqrt(r2), dx, dv);   // two-float mass
             }
         } else {   // FP32
             const float4 *x = reinterpret_cast<const float4 *>(p.js.s[0]);

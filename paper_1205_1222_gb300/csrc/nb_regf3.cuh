@@ -10,8 +10,9 @@
 // both particles, e.g. (x_a, x_b, y_a, y_b), so one 128-bit shared-memory
 // load yields two ready register pairs and no lane ever moves a value into a
 // pair.  The j-tiles flow through an NSTAGE-deep TMA ring without CTA-wide
-// barriers: each warp waits on the stage's full mbarrier, computes, and counts
-// itself out of the stage on a shared counter; the last warp out refills the
+// barriers: each warp waits on the stage's full mbarrier, computes its pair
+// terms, and counts itself out of the stage on a shared counter before its
+// list pass (which reads only flags kept in registers); the last warp out refills the
 // stage with the tile NSTAGE steps ahead (every warp tracks that look-ahead
 // position), so warps drift freely within the ring.  Per-lane float-float
 // totals live in shared memory (folded every FOLD_STEPS_J / _F steps), leaving the
