@@ -19,13 +19,49 @@
 
 namespace nb {
 
+namespace {
+
+// Write this slot's values into float4 k of its j-pair for the NQ streams:
+// stream q holds (v[2q] of both slots, v[2q+1] of both slots).  The even slot
+// writes whole float4s with its partner's values (a shuffle from the next
+// lane); an even slot without a partner in this call, and an odd slot whose
+// partner is not in this call, write their own halves only.
+template <int NQ>
+__device__ __forceinline__ void write_pairs(float4 *const *streams, const float (&v)[2 * NQ], int64_t s, bool live,
+                                            bool even, bool partner_in)
+{
+    const int64_t P = s >> 1;
+    const int lane = threadIdx.x & 31;
+    // the odd slot of a pair whose even slot is outside the call, or in another warp
+    const bool odd_alone = !even && (lane == 0);
+#pragma unroll
+    for (int q = 0; q < NQ; q++) {
+        const float o0 = __shfl_down_sync(0xffffffffu, v[2 * q], 1);
+        const float o1 = __shfl_down_sync(0xffffffffu, v[2 * q + 1], 1);
+        if (!live) continue;
+        if (even && partner_in) {
+            streams[q][P] = make_float4(v[2 * q], o0, v[2 * q + 1], o1);
+        } else if (even || odd_alone) {
+            float *f = reinterpret_cast<float *>(streams[q] + P);
+            const int h = even ? 0 : 1;
+            f[h] = v[2 * q];
+            f[2 + h] = v[2 * q + 1];
+        }
+    }
+}
+
+}  // namespace
+
 __global__ void predict_kernel(const PredParams p)
 {
     const int64_t j = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
-    if (j >= p.n) return;
-    double x[3], v[3];
-    const double m = p.m[j];
-    if (p.a0) {
+    // every lane takes part in the shuffles; lanes past the end only pass values along
+    const bool live = j < p.n;
+    if (!__any_sync(0xffffffffu, live)) return;
+    double x[3] = {0, 0, 0}, v[3] = {0, 0, 0};
+    const double m = live ? p.m[j] : 0.0;
+    if (!live) {
+    } else if (p.a0) {
         const double dt = p.t - p.t0[j];
         for (int k = 0; k < 3; k++) {
             const double x0 = p.x0[3 * j + k], v0 = p.v0[3 * j + k];
@@ -38,10 +74,17 @@ __global__ void predict_kernel(const PredParams p)
         for (int k = 0; k < 3; k++) { x[k] = p.x0[3 * j + k]; v[k] = p.v0[3 * j + k]; }
     }
     const int64_t s = p.offset + j;
-    if (p.forms & 1) {
+    if ((p.forms & 1) && live) {
         p.pos64[s] = make_double4_32a(x[0], x[1], x[2], m);
         p.vel64[s] = make_double4_32a(v[0], v[1], v[2], 0.0);
     }
+    // Pair-interleaved copies: the thread of the even slot of j-pair s / 2
+    // gathers its partner's values with a shuffle and writes whole float4s.
+    // Slots are consecutive across the warp's lanes, and the partner of a
+    // range's last slot (odd offset + n) is outside the range: that half is
+    // left as it is (a later prediction of that slot fills it).
+    const bool even = (s & 1) == 0;
+    const bool partner_in = ((threadIdx.x & 31) + 1 < 32) && (j + 1 < p.n);
     if (p.forms & 2) {
         float xh[3], xl[3], vh[3], vl[3];
         for (int k = 0; k < 3; k++) {
@@ -51,46 +94,26 @@ __global__ void predict_kernel(const PredParams p)
             vl[k] = __double2float_rn(v[k] - static_cast<double>(vh[k]));
         }
         const float mh = __double2float_rn(m);
-        p.mx_hi[s] = make_float4(xh[0], xh[1], xh[2], mh);
-        p.mx_lo[s] = make_float4(xl[0], xl[1], xl[2], __double2float_rn(m - static_cast<double>(mh)));
-        p.mv_hi[s] = make_float4(vh[0], vh[1], vh[2], 0.f);
-        p.mv_lo[s] = make_float4(vl[0], vl[1], vl[2], 0.f);
-    }
-    if (p.forms & 2) {   // pair-interleaved copy: half h of j-pair s / 2
-        const int64_t P = s >> 1;
-        const int h = static_cast<int>(s & 1);
-        float xh[3], xl[3], vh[3], vl[3];
-        for (int k = 0; k < 3; k++) {
-            xh[k] = __double2float_rn(x[k]);
-            xl[k] = __double2float_rn(x[k] - static_cast<double>(xh[k]));
-            vh[k] = __double2float_rn(v[k]);
-            vl[k] = __double2float_rn(v[k] - static_cast<double>(vh[k]));
+        const float ml = __double2float_rn(m - static_cast<double>(mh));
+        if (live) {
+            p.mx_hi[s] = make_float4(xh[0], xh[1], xh[2], mh);
+            p.mx_lo[s] = make_float4(xl[0], xl[1], xl[2], ml);
+            p.mv_hi[s] = make_float4(vh[0], vh[1], vh[2], 0.f);
+            p.mv_lo[s] = make_float4(vl[0], vl[1], vl[2], 0.f);
         }
-        const float vals[14] = {xh[0], xh[1], xh[2], __double2float_rn(m), xl[0], xl[1], xl[2],
+        const float vals[14] = {xh[0], xh[1], xh[2], mh, xl[0], xl[1], xl[2],
                                 vh[0], vh[1], vh[2], vl[0], vl[1], vl[2], 0.f};
-        for (int q = 0; q < 7; q++) {
-            float *f = reinterpret_cast<float *>(p.pim[q] + P);
-            f[h] = vals[2 * q];
-            f[2 + h] = vals[2 * q + 1];
-        }
+        write_pairs<7>(p.pim, vals, s, live, even, partner_in);
     }
     if (p.forms & 4) {
-        const int64_t P = s >> 1;
-        const int h = static_cast<int>(s & 1);
         const float vals[8] = {__double2float_rn(x[0]), __double2float_rn(x[1]), __double2float_rn(x[2]),
                                __double2float_rn(m), __double2float_rn(v[0]), __double2float_rn(v[1]),
                                __double2float_rn(v[2]), 0.f};
-        for (int q = 0; q < 4; q++) {
-            float *f = reinterpret_cast<float *>(p.pif[q] + P);
-            f[h] = vals[2 * q];
-            f[2 + h] = vals[2 * q + 1];
+        if (live) {
+            p.pos32[s] = make_float4(vals[0], vals[1], vals[2], vals[3]);
+            p.vel32[s] = make_float4(vals[4], vals[5], vals[6], 0.f);
         }
-    }
-    if (p.forms & 4) {
-        p.pos32[s] = make_float4(__double2float_rn(x[0]), __double2float_rn(x[1]),
-                                 __double2float_rn(x[2]), __double2float_rn(m));
-        p.vel32[s] = make_float4(__double2float_rn(v[0]), __double2float_rn(v[1]),
-                                 __double2float_rn(v[2]), 0.f);
+        write_pairs<4>(p.pif, vals, s, live, even, partner_in);
     }
 }
 
