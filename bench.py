@@ -238,7 +238,8 @@ class Runner:
         dv = lambda a, dt=torch.float64: torch.as_tensor(np.ascontiguousarray(a), dtype=dt, device=f"cuda:{device}")
         self.d = {k: dv(getattr(w, k)) for k in ("x0", "v0", "a0", "adot0", "m", "t0", "h")}
         self.d["act"] = dv(w.act, torch.int32)
-        self.out = self.ctx.alloc_outputs(w.n_act, w.cap)
+        self.out = self.ctx.alloc_outputs(w.n_act, w.cap, pot=True)
+        self.use_pot = False
         self.stream = torch.cuda.current_stream(device)
         self.form = B.MODE_FORM[self.mode]
         self.launches = 0
@@ -261,7 +262,8 @@ class Runner:
         d, o = self.d, self.out
         self.B.nb_regular_force(self.ctx.h, 0, self.w.n, self.w.n_act, d["act"], d["h"],
                                 d["dtr"] if self.use_dtr else None, self.w.cap,
-                                self.mode, o["F"], o["J"], None, o["nnb"], o["list"], o["ovf"], self.stream)
+                                self.mode, o["F"], o["J"], o["pot"] if self.use_pot else None, o["nnb"], o["list"],
+                                o["ovf"], self.stream)
         self.launches += self.ctx.last_launches()
 
     def timed(self, steps, flush):
@@ -285,7 +287,7 @@ class Runner:
         self.predict()
         t0 = time.perf_counter()
         best, ms = self.ctx.autotune(self.d["act"], self.d["h"], self.w.n, cap=self.w.cap, mode=self.mode,
-                                     dtr=self.d["dtr"] if self.use_dtr else None,
+                                     dtr=self.d["dtr"] if self.use_dtr else None, pot=self.use_pot,
                                      out=self.out, reps=reps, stream=self.stream)
         self.cfg = best.as_tuple()
         return {"best": list(self.cfg), "best_ms": ms, "seconds": time.perf_counter() - t0,
@@ -687,7 +689,8 @@ def run_offset_pairs(args):
 def run_velocity(args):
     """The headline workload with the velocity criterion min(|R|, |R + dtr V|) < h
     (dtr per particle from the regular steps 2^-6 .. 2^-9) against the plain
-    criterion, two-float form, with errors on sampled rows."""
+    criterion, and the plain criterion with the potential output, two-float
+    form, with errors on sampled rows."""
     import numpy as np
     import torch
 
@@ -701,11 +704,12 @@ def run_velocity(args):
     rows = np.sort(np.random.default_rng(7).choice(w.n_act, 2048, replace=False))
     x, v = oracle.predict(w.x0, w.v0, w.a0, w.adot0, w.t0, w.t)
     res = {}
-    for crit in ("plain", "velocity"):
+    for crit in ("plain", "velocity", "plain+potential"):
         o = oracle.regular(x, v, w.m, w.act[rows], w.h[rows], dtr=w.dtr[rows] if crit == "velocity" else None,
-                           cap=w.cap)
+                           cap=w.cap, with_pot=crit.endswith("potential"))
         r = Runner(w, args.mode, 0, "")
         r.use_dtr = crit == "velocity"
+        r.use_pot = crit.endswith("potential")
         if not args.no_tune:
             r.autotune()
         r.predict(); r.force()
@@ -714,12 +718,16 @@ def run_velocity(args):
         r.close()
         res[crit] = {"value": w.n * w.n_act / (ms / 1e3), "kernel_ms": ms, "tiling": r.cfg,
                      "accuracy": accuracy(g, o, rows, w.cap)}
+        if r.use_pot:
+            rp = np.abs(g["pot"][rows] - o["pot"]) / np.abs(o["pot"])
+            res[crit]["accuracy"]["pot_max"] = float(rp.max())
     print(json.dumps({
         "metric": "regular-force interactions/s with the velocity neighbour criterion vs the plain one",
         "unit": "interactions/s", "n_gpus": 1, "dtype": "f32", "data": "synthetic", "mode": args.mode,
         "config": {"workload": "Kroupa-IMF Plummer sphere N=131072, all active, ~100 neighbours, cap 256, seed 3, "
                                "dtr per particle in {2^-6..2^-9}", "oracle_rows": 2048},
         "criteria": res, "cost_of_velocity_criterion": res["velocity"]["kernel_ms"] / res["plain"]["kernel_ms"],
+        "cost_of_potential": res["plain+potential"]["kernel_ms"] / res["plain"]["kernel_ms"],
     }), flush=True)
 
 
