@@ -198,9 +198,13 @@ int entry_occupancy(nb_ctx *ctx, int idx, int *occ)
 }
 
 // Fill the tiling fields of one cluster descriptor.
+// Active particles per i-block of a kernel entry (the list warps of the
+// packed = 6 kernels own none).
+int iblock_size(const KernelEntry &e) { return (e.packed == 6 ? e.warps - 4 : e.warps) * e.ipw; }
+
 void tile_cluster(const KernelEntry &e, int occ, int sm, const nb_kcfg *cfg, ClusterDesc &d)
 {
-    const int ipb = e.warps * e.ipw;
+    const int ipb = iblock_size(e);
     d.n_iblk = (d.n_act + ipb - 1) / ipb;
     d.n_tiles = static_cast<int32_t>((static_cast<int64_t>(d.n_j) + e.jtile - 1) / e.jtile);
     int tps;
@@ -977,7 +981,7 @@ int nb_plan_create(nb_ctx *ctx, int32_t n_clusters, const nb_cluster *cl, int mo
                         mode, cl[c].F, cl[c].J, cl[c].pot, cl[c].nnb, cl[c].list, cl[c].ovf};
         ds.push_back(make_desc(call));
         ClusterDesc &d = ds.back();
-        const int ipb = p->e->warps * p->e->ipw;
+        const int ipb = iblock_size(*p->e);
         d.n_iblk = (d.n_act + ipb - 1) / ipb;
         iblk_total += d.n_iblk;
     }

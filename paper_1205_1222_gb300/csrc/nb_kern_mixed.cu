@@ -16,6 +16,9 @@ static const KernelEntry g_mixed[] = {
     NB_KERNEL_ENTRY5(12, 2, 1024, 4, 0, 1),
     NB_KERNEL_ENTRY5(16, 2, 512, 4, 0, 1),
     NB_KERNEL_ENTRY5(16, 2, 1536, 2, 0, 1),
+    NB_KERNEL_ENTRY6(PairMixedX, 1, 12, 2, 1024, 4, 0),
+    NB_KERNEL_ENTRY6(PairMixedX, 1, 12, 2, 1536, 2, 0),
+    NB_KERNEL_ENTRY6(PairMixedX, 1, 8, 2, 1024, 4, 0),
     NB_KERNEL_ENTRY3(PairMixed, 1, 16, 2, 512, 4, 1, 0, 1),
     NB_KERNEL_ENTRY3(PairMixed, 1, 16, 2, 512, 4, 1, 1, 1),
     NB_KERNEL_ENTRY3(PairMixed, 1, 16, 2, 512, 4, 1, 2, 1),

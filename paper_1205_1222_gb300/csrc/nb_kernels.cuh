@@ -4,6 +4,7 @@
 #include "nb_aux.cuh"
 #include "nb_regf.cuh"
 #include "nb_regf3.cuh"
+#include "nb_regf_ws.cuh"
 
 #define NB_KERNEL_ENTRY(FORM, MODE, W, I, JT, FL)                                       \
     {                                                                                   \
@@ -25,6 +26,15 @@
         1, W, I, JT, FL, 5,                                                             \
             reinterpret_cast<const void *>(&nb::regf3_kernel<nb::PairMixedX, nb::NoFrame, W, I, JT, NST, 1, FL, MINB>), \
             nb::pair_smem_bytes<nb::PairMixedX, W, I, JT, NST>(((FL) & 2) != 0)        \
+    }
+
+// j-pair kernel with WC compute warps and four list warps (packed = 6); the
+// entry's warps field is the CTA's total (WC + 4).
+#define NB_KERNEL_ENTRY6(FORM, MODE, WC, I, JT, NST, FL)                                \
+    {                                                                                   \
+        MODE, (WC) + 4, I, JT, FL, 6,                                                   \
+            reinterpret_cast<const void *>(&nb::regf3ws_kernel<FORM, WC, I, JT, NST, FL>), \
+            nb::ws_smem_bytes<FORM, WC, I, JT, NST>(((FL) & 2) != 0)                   \
     }
 
 // Framed two-float kernel (packed = 4): compact blocks of the spatially sorted
