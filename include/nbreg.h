@@ -86,10 +86,10 @@ typedef struct nb_kcfg {
                          * with the active set sorted along a Morton curve and compact
                          * blocks computed in FP32 offsets from a shared frame centre;
                          * 5 = as 2 (two-float form only) with two-float positions and
-                         * FP32 velocity differences; 6 = the arithmetic of 5 (two-float
-                         * form) or 2 (FP32 form) with `warps` - 4 compute warps and
-                         * one warpgroup of four warps that builds the neighbour
-                         * lists.  FP64 form: 0.                                         */
+                         * FP32 velocity differences; 5 + NL (NL >= 1) = the arithmetic
+                         * of 5 (two-float form) or 2 (FP32 form) with `warps` - NL
+                         * compute warps and NL warps that build the neighbour lists.
+                         * FP64 form: 0.                                                 */
 } nb_kcfg;
 
 /* One independent cluster of a batched call (host struct; the pointers in it

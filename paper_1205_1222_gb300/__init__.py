@@ -71,7 +71,7 @@ class Context:
         n_act = int(act.shape[0])
         out = out or self.alloc_outputs(n_act, cap, pot)
         _b.nb_regular_force(self.h, j_begin, n_j, n_act, act, h, dtr, cap, mode_id(mode), out["F"],
-                            out["J"], out["pot"], out["nnb"], out["list"], out["ovf"], stream)
+                            out["J"], out["pot"] if pot else None, out["nnb"], out["list"], out["ovf"], stream)
         return out
 
     def irregular_force(self, act, nnb, lst, n_j, cap, mode="mixed", j_begin=0, pot=False, stream=None):
@@ -114,4 +114,4 @@ class Context:
         n_act = int(act.shape[0])
         out = out or self.alloc_outputs(n_act, cap, pot)
         return _b.nb_autotune(self.h, j_begin, n_j, n_act, act, h, dtr, cap, mode_id(mode), out["F"], out["J"],
-                              out["pot"], out["nnb"], out["list"], out["ovf"], reps, stream)
+                              out["pot"] if pot else None, out["nnb"], out["list"], out["ovf"], reps, stream)

@@ -198,9 +198,9 @@ int entry_occupancy(nb_ctx *ctx, int idx, int *occ)
 }
 
 // Fill the tiling fields of one cluster descriptor.
-// Active particles per i-block of a kernel entry (the list warps of the
-// packed = 6 kernels own none).
-int iblock_size(const KernelEntry &e) { return (e.packed == 6 ? e.warps - 4 : e.warps) * e.ipw; }
+// Active particles per i-block of a kernel entry (the packed - 5 list warps
+// of the packed >= 6 kernels own none).
+int iblock_size(const KernelEntry &e) { return (e.packed >= 6 ? e.warps - (e.packed - 5) : e.warps) * e.ipw; }
 
 void tile_cluster(const KernelEntry &e, int occ, int sm, const nb_kcfg *cfg, ClusterDesc &d)
 {

@@ -4,13 +4,12 @@
 namespace nb {
 
 static const KernelEntry g_fp32[] = {
+    NB_KERNEL_ENTRY6(PairFP32, 2, 12, 4, 2, 1024, 4, 0),
     NB_KERNEL_ENTRY3(PairFP32, 2, 16, 2, 1024, 4, 1, 0, 1),
     NB_KERNEL_ENTRY3(PairFP32, 2, 16, 2, 1024, 4, 1, 1, 1),
     NB_KERNEL_ENTRY3(PairFP32, 2, 16, 2, 1024, 4, 1, 2, 1),
     NB_KERNEL_ENTRY3(PairFP32, 2, 16, 2, 1024, 4, 1, 3, 1),
     NB_KERNEL_ENTRY3(PairFP32, 2, 16, 2, 2048, 2, 1, 0, 1),
-    NB_KERNEL_ENTRY6(PairFP32, 2, 12, 2, 1024, 4, 0),
-    NB_KERNEL_ENTRY6(PairFP32, 2, 12, 2, 2048, 2, 0),
     NB_KERNEL_ENTRY3(PairFP32, 2, 16, 2, 512, 4, 1, 0, 1),
     NB_KERNEL_ENTRY3(PairFP32, 2, 16, 2, 512, 4, 2, 0, 1),
     NB_KERNEL_ENTRY3(PairFP32, 2, 8, 4, 512, 4, 1, 0, 1),

@@ -1,7 +1,7 @@
 // Compiled configurations of the two-float (NB_MIXED) regular-force kernel:
 // packed f32x2 j-pair kernels (two-float positions with FP32 velocity
-// differences, the default; the exact two-float pair form; the framed form)
-// and the scalar kernel.  The first entry of each
+// differences, with separate list warps (the default) or without; the exact
+// two-float pair form; the framed form) and the scalar kernel.  The first entry of each
 // flag value is the default; all flag-0 entries form the autotuner's search
 // space.
 #include "nb_kernels.cuh"
@@ -9,6 +9,7 @@
 namespace nb {
 
 static const KernelEntry g_mixed[] = {
+    NB_KERNEL_ENTRY6(PairMixedX, 1, 12, 4, 2, 1024, 4, 0),
     NB_KERNEL_ENTRY5(16, 2, 1024, 4, 0, 1),
     NB_KERNEL_ENTRY5(16, 2, 1024, 4, 1, 1),
     NB_KERNEL_ENTRY5(16, 2, 1024, 4, 2, 1),
@@ -16,9 +17,6 @@ static const KernelEntry g_mixed[] = {
     NB_KERNEL_ENTRY5(12, 2, 1024, 4, 0, 1),
     NB_KERNEL_ENTRY5(16, 2, 512, 4, 0, 1),
     NB_KERNEL_ENTRY5(16, 2, 1536, 2, 0, 1),
-    NB_KERNEL_ENTRY6(PairMixedX, 1, 12, 2, 1024, 4, 0),
-    NB_KERNEL_ENTRY6(PairMixedX, 1, 12, 2, 1536, 2, 0),
-    NB_KERNEL_ENTRY6(PairMixedX, 1, 8, 2, 1024, 4, 0),
     NB_KERNEL_ENTRY3(PairMixed, 1, 16, 2, 512, 4, 1, 0, 1),
     NB_KERNEL_ENTRY3(PairMixed, 1, 16, 2, 512, 4, 1, 1, 1),
     NB_KERNEL_ENTRY3(PairMixed, 1, 16, 2, 512, 4, 1, 2, 1),

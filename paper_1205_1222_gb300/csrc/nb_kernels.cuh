@@ -28,13 +28,13 @@
             nb::pair_smem_bytes<nb::PairMixedX, W, I, JT, NST>(((FL) & 2) != 0)        \
     }
 
-// j-pair kernel with WC compute warps and four list warps (packed = 6); the
-// entry's warps field is the CTA's total (WC + 4).
-#define NB_KERNEL_ENTRY6(FORM, MODE, WC, I, JT, NST, FL)                                \
+// j-pair kernel with WC compute warps and NL list warps (packed = 5 + NL); the
+// entry's warps field is the CTA's total (WC + NL).
+#define NB_KERNEL_ENTRY6(FORM, MODE, WC, NL, I, JT, NST, FL)                            \
     {                                                                                   \
-        MODE, (WC) + 4, I, JT, FL, 6,                                                   \
-            reinterpret_cast<const void *>(&nb::regf3ws_kernel<FORM, WC, I, JT, NST, FL>), \
-            nb::ws_smem_bytes<FORM, WC, I, JT, NST>(((FL) & 2) != 0)                   \
+        MODE, (WC) + (NL), I, JT, FL, 5 + (NL),                                         \
+            reinterpret_cast<const void *>(&nb::regf3ws_kernel<FORM, WC, NL, I, JT, NST, FL>), \
+            nb::ws_smem_bytes<FORM, WC, NL, I, JT, NST>(((FL) & 2) != 0)               \
     }
 
 // Framed two-float kernel (packed = 4): compact blocks of the spatially sorted

@@ -1,12 +1,12 @@
-// j-pair regular-force kernel with separate list warps (tiling packed = 6).
+// j-pair regular-force kernel with separate list warps (tiling packed = 5 + NL).
 //
 // The same pair arithmetic as regf3_kernel (Sec. 3.3 step (vi), criterion of
 // Sec. 3.2), but the CTA's warps are specialised: WC compute warps run the
 // pair terms of their i-particles over the j-tiles (the TMA ring, the FP32
 // partials and the float-float totals of regf3_kernel) and hand each tile's
-// neighbour flags to shared memory; one warpgroup of four list warps turns
+// neighbour flags to shared memory; NL list warps turn
 // those flags into the ascending neighbour lists (ballot + popc, as in
-// regf3_kernel) and writes the counts.  The compute warps thus never stop for
+// regf3_kernel) and write the counts.  The compute warps thus never stop for
 // the list compaction, which in regf3_kernel keeps the FMA pipe idle while
 // every warp of a scheduler compacts its lists.  Flags pass through an FR-slot
 // ring: a compute warp waits until the list warps have emptied the slot it
@@ -18,9 +18,9 @@
 
 namespace nb {
 
-template <class Fm, int WC, int I, int JT, int NST_, int FR_ = 2>
+template <class Fm, int WC, int NL, int I, int JT, int NST_, int FR_ = 2>
 struct WsLayout {
-    static constexpr int W = WC + 4;
+    static constexpr int W = WC + NL;
     static constexpr int NST = NST_;
     static constexpr int FR = FR_;
     static constexpr int NP = JT / 2;
@@ -38,17 +38,17 @@ struct WsLayout {
     }
 };
 
-template <class Fm, int WC, int I, int JT, int NST>
+template <class Fm, int WC, int NL, int I, int JT, int NST>
 constexpr int ws_smem_bytes(bool pot)
 {
-    return WsLayout<Fm, WC, I, JT, NST>::bytes(pot);
+    return WsLayout<Fm, WC, NL, I, JT, NST>::bytes(pot);
 }
 
-template <class Fm, int WC, int I, int JT, int NSTAGE, int FLAGS>
-__global__ void __launch_bounds__((WC + 4) * 32, 1) regf3ws_kernel(const RegfParams p)
+template <class Fm, int WC, int NL, int I, int JT, int NSTAGE, int FLAGS>
+__global__ void __launch_bounds__((WC + NL) * 32, 1) regf3ws_kernel(const RegfParams p)
 {
-    static_assert(WC % 4 == 0, "compute warps come in whole warpgroups");
-    using L = WsLayout<Fm, WC, I, JT, NSTAGE>;
+    static_assert(WC % NL == 0, "each list warp serves the same number of compute warps");
+    using L = WsLayout<Fm, WC, NL, I, JT, NSTAGE>;
     using P = Fm;
     using JP = typename P::JP;
     using IB = typename P::IB;
@@ -65,7 +65,7 @@ __global__ void __launch_bounds__((WC + 4) * 32, 1) regf3ws_kernel(const RegfPar
     using Bits = typename std::conditional<2 * STEPS <= 32, uint32_t, uint64_t>::type;
     static_assert(sizeof(Bits) == L::FLB, "flag words");
     static_assert(8 * NST + 16 * FR + 4 * NST <= L::HDR, "barriers and counters fit the header");
-    constexpr int NCW = WC / 4;                                   // compute warps per list warp
+    constexpr int NCW = WC / NL;                                  // compute warps per list warp
 
     extern __shared__ __align__(128) unsigned char smem[];
     uint64_t *full = reinterpret_cast<uint64_t *>(smem);          // tile landed (TMA)
@@ -89,7 +89,7 @@ __global__ void __launch_bounds__((WC + 4) * 32, 1) regf3ws_kernel(const RegfPar
         }
         for (int f = 0; f < FR; f++) {
             mbar_init(&flag_full[f], WC);
-            mbar_init(&flag_empty[f], 4);
+            mbar_init(&flag_empty[f], NL);
         }
         fence_mbar_init();
         TileCursor c0 = la;
@@ -252,7 +252,7 @@ __global__ void __launch_bounds__((WC + 4) * 32, 1) regf3ws_kernel(const RegfPar
         }
     } else {
         // --------------------------------------------------------------- list warps
-        const int lw = warp - WC;   // serves compute warps lw, lw + 4, lw + 8, ...
+        const int lw = warp - WC;   // serves compute warps lw, lw + NL, lw + 2 NL, ...
         for (int64_t item = blockIdx.x; item < p.n_items && !aborted; item += gridDim.x) {
             if (lane == 0) d = p.table ? p.table[find_cluster(p, item)] : p.d0;
             __syncwarp();
@@ -267,7 +267,7 @@ __global__ void __launch_bounds__((WC + 4) * 32, 1) regf3ws_kernel(const RegfPar
             for (int c = 0; c < NCW; c++) {
 #pragma unroll
                 for (int q = 0; q < I; q++) {
-                    const int slot_i = (ib * WC + lw + 4 * c) * I + q;
+                    const int slot_i = (ib * WC + lw + NL * c) * I + q;
                     int a = -1, idx = -1;
                     if (slot_i < d.n_act) {
                         const int aa = d.act[slot_i];
@@ -291,7 +291,7 @@ __global__ void __launch_bounds__((WC + 4) * 32, 1) regf3ws_kernel(const RegfPar
                 for (int c = 0; c < NCW; c++) {
 #pragma unroll
                     for (int q = 0; q < I; q++) {
-                        const Bits b = s_fl[((fs * WC + lw + 4 * c) * I + q) * 32 + lane];
+                        const Bits b = s_fl[((fs * WC + lw + NL * c) * I + q) * 32 + lane];
                         Bits todo = reduce_or_bits(b);
                         while (todo) {
                             const int unit = lowest_bit(todo) >> 1;

@@ -407,10 +407,12 @@ def test_framed_two_float_kernel(offset, pairs):
 
 def test_default_mixed_kernel_is_two_float_positions(cfg2):
     """Unless configured otherwise, two-float calls run the j-pair kernel with
-    two-float positions and FP32 velocity differences (tiling packed = 5)."""
+    two-float positions and FP32 velocity differences and four list warps
+    (tiling packed = 5 + 4)."""
     with Context(cfg2.n) as ctx:
         g = gpu_run(cfg2, "mixed", ctx=ctx)
-        assert ctx.active_config("mixed").packed == 5
+        c = ctx.active_config("mixed")
+        assert c.packed == 9 and c.warps == 16
     assert g["launches"] <= 2          # the force kernel (and the merge of j-splits), no sort
     compare(g, oracle_run(cfg2), cfg2.cap, "mixed")
 
