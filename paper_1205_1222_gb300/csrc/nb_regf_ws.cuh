@@ -11,7 +11,10 @@
 // every warp of a scheduler compacts its lists.  Flags pass through an FR-slot
 // ring: a compute warp waits until the list warps have emptied the slot it
 // fills (flag_empty), the list warps wait until every compute warp has filled
-// it (flag_full).  All waits are bounded.
+// it (flag_full).  The j-tile ring is refilled by list warp 0: a compute warp
+// only arrives on the stage's `empty` barrier when its pair terms are done,
+// and list warp 0 waits for that barrier and issues the copy NST tiles ahead.
+// All waits are bounded.
 #pragma once
 
 #include "nb_regf3.cuh"
@@ -64,14 +67,14 @@ __global__ void __launch_bounds__((WC + NL) * 32, 1) regf3ws_kernel(const RegfPa
     constexpr int FOLD_TILES_F = STEPS >= FOLD_STEPS_F ? 1 : FOLD_STEPS_F / STEPS;
     using Bits = typename std::conditional<2 * STEPS <= 32, uint32_t, uint64_t>::type;
     static_assert(sizeof(Bits) == L::FLB, "flag words");
-    static_assert(8 * NST + 16 * FR + 4 * NST <= L::HDR, "barriers and counters fit the header");
+    static_assert(16 * NST + 16 * FR <= L::HDR, "barriers fit the header");
     constexpr int NCW = WC / NL;                                  // compute warps per list warp
 
     extern __shared__ __align__(128) unsigned char smem[];
     uint64_t *full = reinterpret_cast<uint64_t *>(smem);          // tile landed (TMA)
-    uint64_t *flag_full = full + NST;                             // every compute warp wrote its flags
+    uint64_t *empty = full + NST;                                 // every compute warp is done with the stage
+    uint64_t *flag_full = empty + NST;                            // every compute warp wrote its flags
     uint64_t *flag_empty = flag_full + FR;                        // every list warp read them
-    int *rel = reinterpret_cast<int *>(flag_empty + FR);          // compute warps done with the stage
     unsigned char *stages = smem + L::HDR;
     float2 *s_tot = reinterpret_cast<float2 *>(smem + L::TOT);
     Bits *s_fl = reinterpret_cast<Bits *>(smem + L::fl(POT));     // [FR][WC][I][32]
@@ -85,7 +88,7 @@ __global__ void __launch_bounds__((WC + NL) * 32, 1) regf3ws_kernel(const RegfPa
     if (tid == 0) {
         for (int s = 0; s < NST; s++) {
             mbar_init(&full[s], 1);
-            rel[s] = 0;
+            mbar_init(&empty[s], WC);
         }
         for (int f = 0; f < FR; f++) {
             mbar_init(&flag_full[f], WC);
@@ -98,7 +101,8 @@ __global__ void __launch_bounds__((WC + NL) * 32, 1) regf3ws_kernel(const RegfPa
             cursor_next(p, c0);
         }
     }
-    for (int q = 0; q < NST && la.item < p.n_items; ++q) cursor_next(p, la);   // look-ahead = sequence NST
+    uint32_t issued = 0;   // tiles issued so far (the prologue's, then list warp 0's)
+    for (int q = 0; q < NST && la.item < p.n_items; ++q, ++issued) cursor_next(p, la);   // look-ahead = sequence NST
     __syncthreads();
 
     uint32_t g = 0;
@@ -174,16 +178,9 @@ __global__ void __launch_bounds__((WC + NL) * 32, 1) regf3ws_kernel(const RegfPa
 #pragma unroll 1
                     for (int k = 0; k < STEPS; ++k) step(k, std::true_type{});
                 }
-                // count this warp out of the stage; the last compute warp refills it
+                // this warp is done with the stage; list warp 0 refills it
                 __syncwarp();
-                if (lane == 0) {
-                    __threadfence_block();
-                    if (atomicAdd(&rel[s], 1) == WC - 1) {
-                        rel[s] = 0;
-                        if (la.item < p.n_items) issue_pairs<Fm, JT, NST>(p, la, g + NST, full, stages);
-                    }
-                }
-                cursor_next(p, la);
+                if (lane == 0) mbar_arrive(&empty[s]);
                 // hand the flags to the list warps
                 const uint32_t fs = g % FR;
                 if (!mbar_wait_bounded(&flag_empty[fs], ((g / FR) & 1) ^ 1, p.wait_ns)) { aborted = true; break; }
@@ -246,10 +243,7 @@ __global__ void __launch_bounds__((WC + NL) * 32, 1) regf3ws_kernel(const RegfPa
             }
             __syncwarp();
         }
-        if (aborted && lane == 0) {
-            atomicOr(p.status, DEV_TIMEOUT);
-            for (uint32_t q = g; q < g + NST; ++q) mbar_wait_bounded(&full[q % NST], (q / NST) & 1, p.wait_ns);
-        }
+        if (aborted && lane == 0) atomicOr(p.status, DEV_TIMEOUT);
     } else {
         // --------------------------------------------------------------- list warps
         const int lw = warp - WC;   // serves compute warps lw, lw + NL, lw + 2 NL, ...
@@ -286,6 +280,20 @@ __global__ void __launch_bounds__((WC + NL) * 32, 1) regf3ws_kernel(const RegfPa
             for (int t = tb; t < te; ++t, ++g) {
                 const uint32_t fs = g % FR;
                 if (!mbar_wait_bounded(&flag_full[fs], (g / FR) & 1, p.wait_ns)) { aborted = true; break; }
+                if (lw == 0) {   // refill the stage of tile g with tile g + NST once every compute warp left it
+                    if (lane == 0) {
+                        const int s = g % NST;
+                        if (!mbar_wait_bounded(&empty[s], (g / NST) & 1, p.wait_ns)) {
+                            aborted = true;
+                        } else if (la.item < p.n_items) {
+                            issue_pairs<Fm, JT, NST>(p, la, g + NST, full, stages);
+                            issued = g + NST + 1;
+                        }
+                    }
+                    aborted = __shfl_sync(0xffffffffu, aborted, 0);
+                    if (aborted) break;
+                    cursor_next(p, la);
+                }
                 const int jt0 = t * JT;
 #pragma unroll
                 for (int c = 0; c < NCW; c++) {
@@ -332,7 +340,13 @@ __global__ void __launch_bounds__((WC + NL) * 32, 1) regf3ws_kernel(const RegfPa
             }
             __syncwarp();
         }
-        if (aborted && lane == 0) atomicOr(p.status, DEV_TIMEOUT);
+        if (aborted && lane == 0) {
+            atomicOr(p.status, DEV_TIMEOUT);
+            // let the copies this CTA issued land before its shared memory goes away
+            if (lw == 0)
+                for (uint32_t q = issued > NST ? issued - NST : 0; q < issued; ++q)
+                    mbar_wait_bounded(&full[q % NST], (q / NST) & 1, p.wait_ns);
+        }
     }
 }
 
