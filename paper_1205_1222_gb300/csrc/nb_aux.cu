@@ -185,7 +185,10 @@ __global__ void merge_kernel(const MergeParams p)
 void launch_predict(const PredParams &p, cudaStream_t st)
 {
     if (p.n <= 0) return;
-    const int threads = 256;
+    // The polynomial and the two-float splits run on the FP64 pipe (two lanes
+    // per SM per clock on this part), so a call is bound by the SMs it reaches:
+    // small blocks spread a 16384-slot call over every SM instead of 64 of them.
+    const int threads = 64;
     const int64_t blocks = (p.n + threads - 1) / threads;
     predict_kernel<<<static_cast<unsigned>(blocks), threads, 0, st>>>(p);
 }
