@@ -287,6 +287,36 @@ class Runner:
         force_ms = [e[1].elapsed_time(e[2]) for e in ev]
         return step_ms, force_ms
 
+    def graph_step_us(self, reps=20):
+        """Device time per step of `reps` steps (prediction + force) captured in
+        one CUDA graph and replayed back to back (L2 warm, no host launches):
+        the floor a compiled caller's block step reaches.  Minimum of 3 replays."""
+        torch = self.torch
+        side = torch.cuda.Stream(self.device)
+        side.wait_stream(torch.cuda.current_stream(self.device))
+        old, launches = self.stream, self.launches
+        self.stream = side
+        try:
+            g = torch.cuda.CUDAGraph()
+            with torch.cuda.stream(side):
+                self.predict(); self.force()   # split scratch reserved before the capture
+                torch.cuda.synchronize(self.device)
+                with torch.cuda.graph(g, stream=side):
+                    for _ in range(reps):
+                        self.predict(); self.force()
+            g.replay()
+            torch.cuda.synchronize(self.device)
+            best = float("inf")
+            for _ in range(3):
+                a = torch.cuda.Event(enable_timing=True)
+                b = torch.cuda.Event(enable_timing=True)
+                a.record(); g.replay(); b.record()
+                torch.cuda.synchronize(self.device)
+                best = min(best, a.elapsed_time(b) * 1e3 / reps)
+            return best
+        finally:
+            self.stream, self.launches = old, launches
+
     def autotune(self, reps=1):
         """Native autotuner on this workload (untimed); later calls use its choice."""
         from paper_1205_1222_gb300 import autotune
@@ -817,8 +847,10 @@ def run_blockstep(args):
                 r.predict(); r.force()
             step_ms, force_ms = r.timed(max(3, min(args.steps, 10)), flush)
             g = r.outputs()
+            graph_us = r.graph_step_us()
             r.close()
             row[mode] = {"step_ms": statistics.mean(step_ms), "kernel_ms": statistics.mean(force_ms),
+                         "graph_step_us": graph_us,
                          "interactions_per_s": w.n * n_act / (statistics.mean(step_ms) / 1e3), "tiling": r.cfg,
                          "accuracy": accuracy(g, o, np.arange(n_act), w.cap)}
         res.append(row)
@@ -826,7 +858,8 @@ def run_blockstep(args):
         "metric": "regular-force interactions/s per block step (prediction included) across active-set sizes",
         "unit": "interactions/s", "n_gpus": 1, "dtype": "f32/f64", "data": "synthetic",
         "config": {"workload": "equal-mass Plummer N=16384, seed 2, ~64 neighbours, cap 256, random active subsets",
-                   "l2": "flushed between timed steps"},
+                   "l2": "flushed between timed steps; graph_step_us: 20 steps replayed from one CUDA graph, "
+                         "L2 warm"},
         "sizes": res,
     }), flush=True)
 
