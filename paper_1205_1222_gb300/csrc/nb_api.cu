@@ -436,6 +436,7 @@ int run_single(nb_ctx *ctx, const Call &c, const nb_kcfg *cfg_override, cudaStre
         mp.d0 = d;
         mp.n_clusters = 1;
         mp.n_total = d.n_act;
+        mp.ff = c.mode != NB_FP64;
         nb::launch_merge(mp, st);
         NB_CUDA(ctx, cudaGetLastError());
         ctx->last_launches = 2 + sort_launches;
@@ -1091,6 +1092,7 @@ int nb_plan_run(nb_plan *p, nb_stream_t stream)
         mp.cluster_of = p->d_cluster_of;
         mp.n_clusters = p->n_merge;
         mp.n_total = p->merge_total;
+        mp.ff = p->mode != NB_FP64;
         nb::launch_merge(mp, st);
         NB_CUDA(ctx, cudaGetLastError());
     }
@@ -1249,6 +1251,7 @@ extern "C" int nb_regular_force_noalloc(nb_ctx *ctx, int64_t j_begin, int64_t n_
         mp.d0 = d;
         mp.n_clusters = 1;
         mp.n_total = d.n_act;
+        mp.ff = c.mode != NB_FP64;
         nb::launch_merge(mp, st);
         NB_CUDA(ctx, cudaGetLastError());
         ctx->last_launches = 2;

@@ -9,8 +9,9 @@
 //    also written pair-interleaved (float4 k of j-pair P holds components of
 //    slots 2P and 2P+1) for the j-pair packed kernels.
 //  * merge_kernel: one warp per active particle of a cluster whose j-range
-//    was split over several work items; sums the per-split FP64 partial
-//    force, jerk and potential in a fixed order and concatenates the
+//    was split over several work items; sums the per-split partial force,
+//    jerk and potential in a fixed order (float-float pairs for the float
+//    forms, on the FP32 pipe; FP64 for the FP64 form) and concatenates the
 //    per-split partial lists in split order (ascending j), keeping the first
 //    `cap` entries (Sec. 3.4: force reduction and list gathering kernels).
 #include <cstdint>
@@ -139,14 +140,23 @@ __global__ void merge_kernel(const MergeParams p)
     const int S = d.n_split;
     const int64_t na = d.n_act;
     double sum[7] = {0, 0, 0, 0, 0, 0, 0};
+    float sh[7] = {0, 0, 0, 0, 0, 0, 0}, sl[7] = {0, 0, 0, 0, 0, 0, 0};
     int running = 0;
     for (int s0 = 0; s0 < S; s0 += 32) {
         const int s = s0 + lane;
         int c = 0;
         if (s < S) {
             c = d.pcnt[s * na + i];
-            const double *q = d.pF + (s * na + i) * 8;
-            for (int k = 0; k < 7; k++) sum[k] += q[k];
+            if (p.ff) {
+                const float2 *q = reinterpret_cast<const float2 *>(d.pF + (s * na + i) * 8);
+                for (int k = 0; k < 7; k++) {
+                    const float2 v = q[k];
+                    ff_add_ff(sh[k], sl[k], v.x, v.y);
+                }
+            } else {
+                const double *q = d.pF + (s * na + i) * 8;
+                for (int k = 0; k < 7; k++) sum[k] += q[k];
+            }
         }
         int incl = c;
         for (int o = 1; o < 32; o <<= 1) {
@@ -172,11 +182,32 @@ __global__ void merge_kernel(const MergeParams p)
         }
         running += total;
     }
-    for (int o = 16; o > 0; o >>= 1)
-        for (int k = 0; k < 7; k++) sum[k] += __shfl_xor_sync(0xffffffffu, sum[k], o);
+    if (p.ff) {
+        // float-float butterfly, then lane k < 7 converts component k: one FP64
+        // add per lane instead of 35 on every lane (GB300's FP64 pipe is narrow)
+        for (int o = 16; o > 0; o >>= 1)
+            for (int k = 0; k < 7; k++) {
+                const float h2 = __shfl_xor_sync(0xffffffffu, sh[k], o);
+                const float l2 = __shfl_xor_sync(0xffffffffu, sl[k], o);
+                ff_add_ff(sh[k], sl[k], h2, l2);
+            }
+        float h = 0.f, l = 0.f;
+#pragma unroll
+        for (int k = 0; k < 7; k++)
+            if (k == lane) { h = sh[k]; l = sl[k]; }
+        const double v = static_cast<double>(h) + static_cast<double>(l);
+        if (lane < 3) d.F[3 * i + lane] = v;
+        else if (lane < 6) d.J[3 * i + lane - 3] = v;
+        else if (lane == 6 && d.pot) d.pot[i] = v;
+    } else {
+        for (int o = 16; o > 0; o >>= 1)
+            for (int k = 0; k < 7; k++) sum[k] += __shfl_xor_sync(0xffffffffu, sum[k], o);
+        if (lane == 0) {
+            for (int k = 0; k < 3; k++) { d.F[3 * i + k] = sum[k]; d.J[3 * i + k] = sum[3 + k]; }
+            if (d.pot) d.pot[i] = sum[6];
+        }
+    }
     if (lane == 0) {
-        for (int k = 0; k < 3; k++) { d.F[3 * i + k] = sum[k]; d.J[3 * i + k] = sum[3 + k]; }
-        if (d.pot) d.pot[i] = sum[6];
         d.nnb[i] = running;
         d.ovf[i] = running > d.cap ? 1 : 0;
     }
@@ -196,7 +227,8 @@ void launch_predict(const PredParams &p, cudaStream_t st)
 void launch_merge(const MergeParams &p, cudaStream_t st)
 {
     if (p.n_total <= 0) return;
-    const int threads = 256;
+    // one warp per block: a small merge spreads over as many SMs as it has particles
+    const int threads = 32;
     const int64_t blocks = (p.n_total * 32 + threads - 1) / threads;
     merge_kernel<<<static_cast<unsigned>(blocks), threads, 0, st>>>(p);
 }

@@ -28,6 +28,7 @@ struct MergeParams {
     const int32_t *cluster_of;     // [n_clusters] index into table of each merged cluster
     int32_t n_clusters;            // merged clusters
     int64_t n_total;               // total merged active particles (one warp each)
+    int ff;                        // 1: split slots hold float-float pairs (float forms), 0: doubles (FP64 form)
 };
 
 void launch_predict(const PredParams &p, cudaStream_t st);

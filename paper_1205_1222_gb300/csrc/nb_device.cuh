@@ -172,6 +172,58 @@ __device__ __forceinline__ void ff_add_ff(float &hi, float &lo, float h2, float 
     lo = __fsub_rn(e, __fsub_rn(hi, s));
 }
 
+// End of a work item in the float forms.  After the float-float totals of the
+// warp's I particles are reduced over the lanes (every lane then holds all of
+// them), lane 8q + c (mod 32; round (8q + c) / 32) keeps component c (F 0..2,
+// J 3..5, potential 6) of particle q with ff_keep, and write_item_ff stores it:
+// in FP64 to the outputs when the call is not split, else as the float-float
+// pair itself into the (split, particle) slot of the split scratch
+// (components NC..6 as zeros), which the merge sums in float-float.  So one
+// FP64 conversion per lane replaces one per component on every lane: the FP64
+// pipe (about two lanes per SM per clock on GB300) would otherwise hold every
+// warp of the SM for ~1 us at the end of each item.
+template <int I>
+struct FFKeep {
+    static constexpr int R = (8 * I + 31) / 32;   // rounds of 32 (particle, component) slots
+    float h[R], l[R];
+};
+
+template <int I>
+__device__ __forceinline__ void ff_keep(FFKeep<I> &k, int q, int c, float hi, float lo)
+{
+    const int slot = 8 * q + c;   // q, c are compile-time after unrolling
+    if ((threadIdx.x & 31) == (slot & 31)) { k.h[slot >> 5] = hi; k.l[slot >> 5] = lo; }
+}
+
+template <int I, int NC>
+__device__ __forceinline__ void write_item_ff(const ClusterDesc &d, int sp, const FFKeep<I> &k, const int (&oi)[I])
+{
+    static_assert(NC <= 7, "F, J and the potential");
+    const int lane = threadIdx.x & 31;
+    const int c = lane & 7;
+#pragma unroll
+    for (int r = 0; r < FFKeep<I>::R; r++) {
+        const int q = 4 * r + (lane >> 3);
+        int i = -1;
+#pragma unroll
+        for (int qq = 4 * r; qq < I && qq < 4 * r + 4; qq++)
+            if (qq == q) i = oi[qq];
+        if (q >= I || i < 0 || c >= 7) continue;
+        const int64_t ii = i;
+        const float h = c < NC ? k.h[r] : 0.f, l = c < NC ? k.l[r] : 0.f;
+        if (d.n_split == 1) {
+            if (c >= NC) continue;
+            const double v = static_cast<double>(h) + static_cast<double>(l);
+            if (c < 3) d.F[3 * ii + c] = v;
+            else if (c < 6) d.J[3 * ii + c - 3] = v;
+            else if (d.pot) d.pot[ii] = v;
+        } else {
+            float2 *slot = reinterpret_cast<float2 *>(d.pF + (static_cast<int64_t>(sp) * d.n_act + ii) * 8);
+            slot[c] = make_float2(h, l);
+        }
+    }
+}
+
 __device__ __forceinline__ unsigned lanemask_lt()
 {
     unsigned m;

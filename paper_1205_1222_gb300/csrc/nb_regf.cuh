@@ -423,40 +423,57 @@ __global__ void __launch_bounds__(W * 32) regf_kernel(const RegfParams p)
         if (aborted) break;
 
         // reduce over the 32 lanes and write
+        if constexpr (Fm::F64) {
 #pragma unroll
-        for (int k = 0; k < I; k++) {
-            double out[7];
-            if (Fm::F64) {
+            for (int k = 0; k < I; k++) {
+                double out[7];
                 for (int c = 0; c < 3; c++) { out[c] = acc[k].f[c]; out[3 + c] = acc[k].j[c]; }
                 out[6] = acc[k].p;
                 for (int o = 16; o > 0; o >>= 1)
                     for (int c = 0; c < 7; c++) out[c] += __shfl_xor_sync(0xffffffffu, out[c], o);
-            } else {
+                if (lane == 0 && idx[k] >= 0) {
+                    const int64_t i = idx[k];
+                    if (d.n_split == 1) {
+                        for (int c = 0; c < 3; c++) { d.F[3 * i + c] = out[c]; d.J[3 * i + c] = out[3 + c]; }
+                        if (POT && d.pot) d.pot[i] = out[6];
+                    } else {
+                        double *q = d.pF + (static_cast<int64_t>(sp) * d.n_act + i) * 8;
+                        for (int c = 0; c < 7; c++) q[c] = POT || c < 6 ? out[c] : 0.0;
+                    }
+                }
+            }
+        } else {
+            constexpr int NC = POT ? 7 : 6;
+            FFKeep<I> kept{};
+#pragma unroll
+            for (int k = 0; k < I; k++) {
                 float hi[7], lo[7];
                 for (int c = 0; c < 3; c++) {
                     hi[c] = tot[k].fh[c]; lo[c] = tot[k].fl[c];
                     hi[3 + c] = tot[k].jh[c]; lo[3 + c] = tot[k].jl[c];
                 }
                 hi[6] = tot[k].ph; lo[6] = tot[k].pl;
-                for (int o = 16; o > 0; o >>= 1)
-                    for (int c = 0; c < 7; c++) {
-                        if (c == 6 && !POT) continue;
+                for (int o = 16; o > 0; o >>= 1) {
+#pragma unroll
+                    for (int c = 0; c < NC; c++) {
                         const float h2 = __shfl_xor_sync(0xffffffffu, hi[c], o);
                         const float l2 = __shfl_xor_sync(0xffffffffu, lo[c], o);
                         ff_add_ff(hi[c], lo[c], h2, l2);
                     }
-                for (int c = 0; c < 7; c++) out[c] = static_cast<double>(hi[c]) + static_cast<double>(lo[c]);
+                }
+#pragma unroll
+                for (int c = 0; c < NC; c++) ff_keep(kept, k, c, hi[c], lo[c]);
             }
+            write_item_ff<I, NC>(d, sp, kept, idx);
+        }
+#pragma unroll
+        for (int k = 0; k < I; k++) {
             if (lane == 0 && idx[k] >= 0) {
                 const int64_t i = idx[k];
                 if (d.n_split == 1) {
-                    for (int c = 0; c < 3; c++) { d.F[3 * i + c] = out[c]; d.J[3 * i + c] = out[3 + c]; }
-                    if (POT && d.pot) d.pot[i] = out[6];
                     d.nnb[i] = cnt[k];
                     d.ovf[i] = cnt[k] > d.cap ? 1 : 0;
                 } else {
-                    double *q = d.pF + (static_cast<int64_t>(sp) * d.n_act + i) * 8;
-                    for (int c = 0; c < 7; c++) q[c] = POT || c < 6 ? out[c] : 0.0;
                     d.pcnt[static_cast<int64_t>(sp) * d.n_act + i] = cnt[k];
                 }
             }

@@ -596,9 +596,10 @@ __global__ void __launch_bounds__(W * 32, MINB) regf3_kernel(const RegfParams p)
         if (aborted) return;
 
         // reduce the float-float totals over the 32 lanes, then write
+        FFKeep<I> kept{};
 #pragma unroll
         for (int q = 0; q < I; q++) {
-            double out[7] = {0, 0, 0, 0, 0, 0, 0};
+#pragma unroll
             for (int c = 0; c < NC; c++) {
                 const float2 v = mytot[(q * NC + c) * 32];
                 float hi = v.x, lo = v.y;
@@ -607,19 +608,19 @@ __global__ void __launch_bounds__(W * 32, MINB) regf3_kernel(const RegfParams p)
                     const float l2 = __shfl_xor_sync(0xffffffffu, lo, o);
                     ff_add_ff(hi, lo, h2, l2);
                 }
-                out[c] = static_cast<double>(hi) + static_cast<double>(lo);
+                ff_keep(kept, q, c, hi, lo);
             }
+        }
+        write_item_ff<I, NC>(d, sp, kept, oidx);
+#pragma unroll
+        for (int q = 0; q < I; q++) {
             const int64_t i = oidx[q];
             if (lane == 0 && i >= 0) {
                 const int nq = cnt[q];
                 if (d.n_split == 1) {
-                    for (int c = 0; c < 3; c++) { d.F[3 * i + c] = out[c]; d.J[3 * i + c] = out[3 + c]; }
-                    if (POT && d.pot) d.pot[i] = out[6];
                     d.nnb[i] = nq;
                     d.ovf[i] = nq > d.cap ? 1 : 0;
                 } else {
-                    double *o8 = d.pF + (static_cast<int64_t>(sp) * d.n_act + i) * 8;
-                    for (int c = 0; c < 7; c++) o8[c] = c < NC ? out[c] : 0.0;
                     d.pcnt[static_cast<int64_t>(sp) * d.n_act + i] = nq;
                 }
             }

@@ -217,6 +217,9 @@ __global__ void __launch_bounds__((WC + NL) * 32, 1) regf3ws_kernel(const RegfPa
 
             // reduce the float-float totals over the 32 lanes, then write F, J (and
             // the potential); the list warps write the counts and lists
+            // (This kernel serves the large calls: its FP64 conversions on every
+            // lane cost little per item there, and the per-lane store of the
+            // other kernels changed its register allocation for the worse.)
 #pragma unroll
             for (int q = 0; q < I; q++) {
                 double out[7] = {0, 0, 0, 0, 0, 0, 0};
@@ -236,8 +239,13 @@ __global__ void __launch_bounds__((WC + NL) * 32, 1) regf3ws_kernel(const RegfPa
                         for (int c = 0; c < 3; c++) { d.F[3 * i + c] = out[c]; d.J[3 * i + c] = out[3 + c]; }
                         if (POT && d.pot) d.pot[i] = out[6];
                     } else {
-                        double *o8 = d.pF + (static_cast<int64_t>(sp) * d.n_act + i) * 8;
-                        for (int c = 0; c < 7; c++) o8[c] = c < NC ? out[c] : 0.0;
+                        // the split slot holds float-float pairs, as written by write_item_ff
+                        float2 *o8 = reinterpret_cast<float2 *>(d.pF + (static_cast<int64_t>(sp) * d.n_act + i) * 8);
+                        for (int c = 0; c < 7; c++) {
+                            const float h = c < NC ? __double2float_rn(out[c]) : 0.f;
+                            const float l = c < NC ? __double2float_rn(out[c] - static_cast<double>(h)) : 0.f;
+                            o8[c] = make_float2(h, l);
+                        }
                     }
                 }
             }
