@@ -326,6 +326,34 @@ def test_host_step_matches_oracle():
     compare(g, oracle_run(w), w.cap, "mixed")
 
 
+def test_host_step_in_chunks_matches_the_device_call():
+    """A large active set goes through nb_step_host in chunks (98304 active on a
+    152-SM GB300: three chunks of 9, 9 and 8.9 rounds of the persistent grid),
+    each chunk's results copied back while the next computes: outputs are
+    bit-identical to one device call on the same inputs, and match the oracle
+    on sampled rows."""
+    import torch
+    w = inputs.cluster(100000, 19, 48, 128, act=np.arange(0, 98304, dtype=np.int32))
+    pin = lambda a, dt=torch.float64: torch.as_tensor(np.ascontiguousarray(a), dtype=dt).pin_memory()
+    hx = {k: pin(getattr(w, k)) for k in ("x0", "v0", "a0", "adot0", "m", "t0", "h")}
+    act = pin(w.act, torch.int32)
+    F = torch.empty((w.n_act, 3), dtype=torch.float64).pin_memory()
+    J = torch.empty_like(F)
+    nnb = torch.empty(w.n_act, dtype=torch.int32).pin_memory()
+    lst = torch.zeros((w.n_act, w.cap), dtype=torch.int32).pin_memory()
+    ovf = torch.empty(w.n_act, dtype=torch.uint8).pin_memory()
+    with Context(w.n) as ctx:
+        B.nb_step_host(ctx.h, w.n, hx["x0"], hx["v0"], hx["a0"], hx["adot0"], hx["m"], hx["t0"], w.t, w.n_act,
+                       act, hx["h"], None, w.cap, B.NB_MIXED, F, J, None, nnb, lst, ovf)
+        assert ctx.last_launches() >= 3, "prediction and at least two force launches"
+        one = gpu_run(w, "mixed", ctx=ctx)
+    g = {"F": F.numpy(), "J": J.numpy(), "nnb": nnb.numpy(), "list": lst.numpy(), "ovf": ovf.numpy()}
+    for k in ("F", "J", "nnb", "list", "ovf"):
+        assert np.array_equal(g[k], one[k]), k
+    rows = np.sort(np.random.default_rng(3).choice(w.n_act, 256, replace=False))
+    compare(g, oracle_run(w, rows=rows), w.cap, "mixed", rows=rows)
+
+
 # ------------------------------------------------- device-side error paths
 
 def test_invalid_device_inputs_are_reported_not_faulted():
