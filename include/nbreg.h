@@ -223,7 +223,10 @@ int nb_plan_launches(const nb_plan *plan);
  * the regular force, copy the results back into host memory and wait for
  * them.  All array arguments are HOST pointers (pinned memory gives
  * asynchronous copies).  List slots past min(nnb, cap) are returned as -1.  Same meaning and errors as nb_predict followed by
- * nb_regular_force on j-range [0, n); also returns the device status. */
+ * nb_regular_force on j-range [0, n); also returns the device status.  A large
+ * active set is computed in a few chunks of consecutive active particles whose
+ * results are copied back while the next chunk computes (same results as one
+ * call). */
 int nb_step_host(nb_ctx *ctx, int64_t n, const double *x0, const double *v0, const double *a0,
                  const double *adot0, const double *m, const double *t0, double t,
                  int32_t n_act, const int32_t *act, const double *h, const double *dtr,

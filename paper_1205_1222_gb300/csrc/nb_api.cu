@@ -918,18 +918,30 @@ int nb_step_host(nb_ctx *ctx, int64_t n, const double *x0, const double *v0, con
         // chunk's copy follows the computation (at N = n_act = 131072 the
         // results are ~140 MB, 0.77 ms over the host link).  Chunks are whole
         // rounds of the persistent grid (resident CTAs x particles per CTA
-        // block), at least 8 each, so that no chunk ends in a part-filled round.
+        // block), so that no chunk ends in a part-filled round: up to three of
+        // at least 8 rounds, then the last round alone, whose copy is the only
+        // one left after the computation.  Every chunk takes the j-split of the
+        // whole call, so the sums, and the results, are those of one call.
         const int flags = (dtr ? 1 : 0) | (pot ? 2 : 0);
-        const nb_kcfg cfg = pick_cfg(ctx, mode, flags, n_act, n);
+        nb_kcfg cfg = pick_cfg(ctx, mode, flags, n_act, n);
         int64_t round = 0;
         {
             const int idx = find_entry(mode, cfg, flags);
             int occ = 0;
-            if (idx >= 0 && entry_occupancy(ctx, idx, &occ) == NB_OK && occ > 0)
-                round = static_cast<int64_t>(ctx->sm_count) * occ * iblock_size(registry().all[idx]);
+            if (idx >= 0 && entry_occupancy(ctx, idx, &occ) == NB_OK && occ > 0) {
+                const KernelEntry &e = registry().all[idx];
+                round = static_cast<int64_t>(ctx->sm_count) * occ * iblock_size(e);
+                ClusterDesc whole{};
+                whole.n_j = static_cast<int32_t>(n);
+                whole.n_act = n_act;
+                whole.cap = cap;
+                tile_cluster(e, occ, ctx->sm_count, &cfg, whole);
+                cfg.split = whole.tiles_per_split;
+            }
         }
         const int64_t rounds = round > 0 ? (n_act + round - 1) / round : 1;
-        const int K = static_cast<int>(std::min<int64_t>(4, std::max<int64_t>(1, rounds / 8)));
+        const int KB = static_cast<int>(std::min<int64_t>(3, (rounds - 1) / 8));   // chunks before the last round
+        const int K = KB > 0 ? KB + 1 : 1;
         if (K > 1 && !ctx->copy_st) {
             NB_CUDA(ctx, cudaStreamCreateWithFlags(&ctx->copy_st, cudaStreamNonBlocking));
             for (cudaEvent_t &e : ctx->chunk_ev) NB_CUDA(ctx, cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
@@ -939,8 +951,8 @@ int nb_step_host(nb_ctx *ctx, int64_t n, const double *x0, const double *v0, con
         const auto ip = [&](size_t o) { return reinterpret_cast<int32_t *>(s + o); };
         const size_t capz = static_cast<size_t>(cap);
         for (int k = 0; k < K; k++) {
-            const int64_t k0 = std::min<int64_t>(n_act, round * (rounds * k / K));
-            const int64_t k1 = k + 1 == K ? n_act : std::min<int64_t>(n_act, round * (rounds * (k + 1) / K));
+            const int64_t k0 = K == 1 ? 0 : round * ((rounds - 1) * std::min(k, KB) / KB);
+            const int64_t k1 = k + 1 == K ? n_act : round * ((rounds - 1) * (k + 1) / KB);
             const size_t c0 = static_cast<size_t>(k0), cn = static_cast<size_t>(k1 - k0);
             const Call c{0, n, static_cast<int32_t>(k1 - k0), ip(o_act) + c0, dp(o_h) + c0,
                          dtr ? dp(o_dtr) + c0 : nullptr, cap, mode, dp(o_F) + 3 * c0, dp(o_J) + 3 * c0,

@@ -328,7 +328,8 @@ def test_host_step_matches_oracle():
 
 def test_host_step_in_chunks_matches_the_device_call():
     """A large active set goes through nb_step_host in chunks (98304 active on a
-    152-SM GB300: three chunks of 9, 9 and 8.9 rounds of the persistent grid),
+    152-SM GB300: chunks of 8, 9 and 9 rounds of the persistent grid, then the
+    last, part-filled round alone),
     each chunk's results copied back while the next computes: outputs are
     bit-identical to one device call on the same inputs, and match the oracle
     on sampled rows."""
