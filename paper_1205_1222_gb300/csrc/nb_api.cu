@@ -213,12 +213,32 @@ void tile_cluster(const KernelEntry &e, int occ, int sm, const nb_kcfg *cfg, Clu
     int tps;
     if (cfg && cfg->split > 0) {
         tps = cfg->split;
-    } else {
-        // enough work items for ~4 resident CTAs' worth of items per slot,
-        // but at least two tiles per item
+    } else if (e.packed < 2) {
+        // scalar kernels: enough work items for ~4 resident CTAs' worth of
+        // items per slot, but at least two tiles per item
         const int64_t slots = static_cast<int64_t>(sm) * occ;
         const int64_t want = std::max<int64_t>(1, (4 * slots + d.n_iblk - 1) / std::max(d.n_iblk, 1));
         tps = static_cast<int>(std::max<int64_t>(2, (d.n_tiles + want - 1) / want));
+    } else {
+        // Packed kernels.  The persistent grid deals the work items round-robin
+        // to its resident CTAs, so a call takes about ceil(items / slots)
+        // rounds of one item's time.  Choose the tiles per split that minimise
+        // that, counting an item's fixed cost (particle loads, lane reduction,
+        // conversion and stores: ~6 us, measured at N = 16384) as 1.5 tiles and
+        // a split call's merge as a launch plus its reads of the partials
+        // (about 2e7 bytes per tile time); on a tie, fewer splits.  The split
+        // scratch stays under 1 GiB.
+        const int64_t slots = std::max<int64_t>(1, static_cast<int64_t>(sm) * occ);
+        double best = 0.0;
+        tps = d.n_tiles;
+        for (int t = d.n_tiles; t >= 1; --t) {
+            const int64_t ns = (d.n_tiles + t - 1) / t;
+            if (ns > 1 && ns * d.n_act * (72 + 4 * static_cast<int64_t>(d.cap)) > (int64_t(1) << 30)) continue;
+            const int64_t rounds = (static_cast<int64_t>(d.n_iblk) * ns + slots - 1) / slots;
+            const double merge = ns > 1 ? 1.5 + static_cast<double>(ns) * d.n_act * (64.0 + 2.0 * d.cap) / 2e7 : 0.0;
+            const double cost = static_cast<double>(rounds) * (t + 1.5) + merge;
+            if (t == d.n_tiles || cost < best - 1e-9) { best = cost; tps = t; }
+        }
     }
     d.tiles_per_split = std::max(1, tps);
     d.n_split = d.n_tiles == 0 ? 1 : (d.n_tiles + d.tiles_per_split - 1) / d.tiles_per_split;
