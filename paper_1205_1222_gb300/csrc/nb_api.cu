@@ -421,6 +421,10 @@ int run_single(nb_ctx *ctx, const Call &c, const nb_kcfg *cfg_override, cudaStre
     int idx = find_entry(c.mode, cfg, flags);
     if (idx < 0) { ctx->err = "no kernel for this mode"; return NB_ERR_UNSUPPORTED; }
     if (registry().all[idx].packed >= 2 && (c.j_begin & 1)) idx = layout_fallback(c.mode, idx, flags);
+    if (registry().all[idx].packed >= 2 && (c.j_begin & 1)) {
+        ctx->err = "no per-particle-layout kernel for a j-range at an odd slot with these flags";
+        return NB_ERR_UNSUPPORTED;
+    }
     int occ = 0;
     rc = entry_occupancy(ctx, idx, &occ);
     if (rc != NB_OK) return rc;
@@ -1043,6 +1047,10 @@ int nb_plan_create(nb_ctx *ctx, int32_t n_clusters, const nb_cluster *cl, int mo
     bool odd = false;
     for (int c = 0; c < n_clusters; c++) odd |= (cl[c].j_begin & 1) != 0;
     if (registry().all[idx].packed >= 2 && odd) idx = layout_fallback(mode, idx, flags);
+    if (registry().all[idx].packed >= 2 && odd) {
+        ctx->err = "no per-particle-layout kernel for a j-range at an odd slot with these flags";
+        return NB_ERR_UNSUPPORTED;
+    }
     int occ = 0;
     int rc = entry_occupancy(ctx, idx, &occ);
     if (rc != NB_OK) return rc;
@@ -1289,6 +1297,10 @@ extern "C" int nb_regular_force_noalloc(nb_ctx *ctx, int64_t j_begin, int64_t n_
     int idx = find_entry(c.mode, cfg, flags);
     if (idx < 0) { ctx->err = "no kernel for this mode"; return NB_ERR_UNSUPPORTED; }
     if (registry().all[idx].packed >= 2 && (c.j_begin & 1)) idx = layout_fallback(c.mode, idx, flags);
+    if (registry().all[idx].packed >= 2 && (c.j_begin & 1)) {
+        ctx->err = "no per-particle-layout kernel for a j-range at an odd slot with these flags";
+        return NB_ERR_UNSUPPORTED;
+    }
     int occ = 0;
     rc = entry_occupancy(ctx, idx, &occ);
     if (rc != NB_OK) return rc;

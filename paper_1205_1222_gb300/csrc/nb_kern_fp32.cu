@@ -16,6 +16,11 @@ static const KernelEntry g_fp32[] = {
     NB_KERNEL_ENTRY(FormFP32, 2, 8, 4, 512, 0),
     NB_KERNEL_ENTRY(FormFP32, 2, 8, 8, 512, 0),
     NB_KERNEL_ENTRY(FormFP32, 2, 8, 2, 512, 0),
+    // per-particle layout with the velocity criterion and/or the potential: the
+    // fallback for a j-range that starts at an odd slot
+    NB_KERNEL_ENTRY(FormFP32, 2, 8, 2, 512, 1),
+    NB_KERNEL_ENTRY(FormFP32, 2, 8, 2, 512, 2),
+    NB_KERNEL_ENTRY(FormFP32, 2, 8, 2, 512, 3),
 };
 
 const KernelEntry *kernels_fp32(int *count)

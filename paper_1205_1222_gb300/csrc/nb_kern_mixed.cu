@@ -33,6 +33,11 @@ static const KernelEntry g_mixed[] = {
     NB_KERNEL_ENTRY(FormMixed, 1, 4, 4, 512, 0),
     NB_KERNEL_ENTRY(FormMixed, 1, 8, 2, 512, 0),
     NB_KERNEL_ENTRY(FormMixed, 1, 16, 2, 512, 0),
+    // per-particle layout with the velocity criterion and/or the potential: the
+    // fallback for a j-range that starts at an odd slot
+    NB_KERNEL_ENTRY(FormMixed, 1, 8, 2, 512, 1),
+    NB_KERNEL_ENTRY(FormMixed, 1, 8, 2, 512, 2),
+    NB_KERNEL_ENTRY(FormMixed, 1, 8, 2, 512, 3),
 };
 
 const KernelEntry *kernels_mixed(int *count)

@@ -159,6 +159,50 @@ def test_j_range_offset_in_a_larger_context():
     compare(g, oracle_run(w), w.cap, "mixed")
 
 
+@pytest.mark.parametrize("mode", ["mixed", "fp32"])
+@pytest.mark.parametrize("vel,pot", [(True, False), (False, True), (True, True)])
+def test_odd_first_slot_with_velocity_criterion_or_potential(mode, vel, pot):
+    """A j-range at an odd slot cannot be read as j-pairs: the call runs on a
+    per-particle-layout kernel compiled with the same flags."""
+    w = inputs.cluster(3000, 31, 40, 64, act=np.arange(0, 3000, 7, dtype=np.int32),
+                       dtr_steps=(2.0**-6, 2.0**-8) if vel else None)
+    with Context(w.n + 3) as ctx:
+        g = gpu_run(w, mode, pot=pot, ctx=ctx, j_offset=3)
+    assert g["status"] == 0
+    compare(g, oracle_run(w, pot=pot), w.cap, mode, pot=pot and mode != "fp32", lists=(mode != "fp32"))
+
+
+def _sweep_cases(count=24, seed=2026):
+    """Seeded random combinations of size, active count, neighbour count, list
+    capacity (0 and overflowing ones included), form, velocity criterion,
+    potential, j-range offset (odd ones take the per-particle layout) and
+    j-split (default tiling, or 1 or 3 tiles per split)."""
+    rng = np.random.default_rng(seed)
+    out = []
+    for k in range(count):
+        n = int(rng.integers(40, 9000))
+        out.append(dict(k=k, n=n, n_act=int(rng.integers(1, n + 1)), k_nb=int(rng.integers(1, min(80, n - 4))),
+                        cap=int(rng.choice([0, 1, 16, 64, 128, 256])), mode=str(rng.choice(["fp64", "mixed", "mixed"])),
+                        vel=bool(rng.random() < 0.4), pot=bool(rng.random() < 0.4),
+                        off=int(rng.choice([0, 0, 1, 2, 777])), split=int(rng.choice([0, 0, 1, 3]))))
+    return out
+
+
+@pytest.mark.parametrize("c", _sweep_cases(), ids=lambda c: f"case{c['k']}-{c['mode']}")
+def test_random_sweep(c):
+    act = np.sort(np.random.default_rng(1000 + c["k"]).choice(c["n"], c["n_act"], replace=False)).astype(np.int32)
+    w = inputs.cluster(c["n"], 500 + c["k"], c["k_nb"], max(c["cap"], 1), act=act,
+                       dtr_steps=(2.0**-6, 2.0**-8) if c["vel"] else None)
+    cfg = None
+    if c["split"]:
+        d = B.nb_get_kernel_config(mode_id(c["mode"]), 0).as_tuple()   # the default tiling
+        cfg = B.nb_kcfg(d[0], d[1], d[2], c["split"], d[4])
+    with Context(c["n"] + c["off"]) as ctx:
+        g = gpu_run(w, c["mode"], cap=c["cap"], pot=c["pot"], ctx=ctx, j_offset=c["off"], cfg=cfg)
+    assert g["status"] == 0
+    compare(g, oracle_run(w, cap=c["cap"], pot=c["pot"]), c["cap"], c["mode"], pot=c["pot"])
+
+
 def test_split_and_unsplit_paths_agree():
     w = inputs.cluster(20000, 14, 64, 256, act=np.arange(0, 20000, 97, dtype=np.int32))
     o = oracle_run(w)
