@@ -350,6 +350,47 @@ def test_batched_plan_and_graph(mode, even):
             B.nb_plan_destroy(plan)
 
 
+@pytest.mark.parametrize("mode,odd", [("mixed", False), ("mixed", True), ("fp64", True)])
+def test_batched_plan_with_mixed_flags(mode, odd):
+    """A plan whose clusters differ in flags: some with the velocity criterion,
+    some with the potential, some with neither.  The plan runs one kernel with
+    the union of the flags; each cluster must still get exactly its own
+    criterion and outputs.  With odd slot offsets the plan takes the
+    per-particle layout."""
+    rng = np.random.default_rng(61)
+    ws, vel, pot = [], [], []
+    for c in range(6):
+        n = int(rng.integers(600, 3000))
+        act = np.sort(rng.choice(n, int(rng.integers(1, n)), replace=False)).astype(np.int32)
+        v, q = c % 3 == 0, c % 2 == 1
+        ws.append(inputs.cluster(n, 900 + c, 40, 64, act=act, dtr_steps=(2.0**-6, 2.0**-8) if v else None))
+        vel.append(v)
+        pot.append(q)
+    offs = np.cumsum([0] + [w.n + 5 for w in ws])
+    offs = offs + 1 if odd else offs + (offs % 2)
+    with Context(int(offs[-1])) as ctx:
+        keep, cl = [], []
+        for w, off, q in zip(ws, offs, pot):
+            d = upload(w)
+            ctx.predict(d["x0"], d["v0"], d["a0"], d["adot0"], d["m"], d["t0"], w.t, offset=int(off))
+            out = ctx.alloc_outputs(w.n_act, w.cap, pot=q)
+            keep.append((d, out))
+            cl.append(B.nb_cluster(int(off), w.n, w.n_act, w.cap, d["act"].data_ptr(), d["h"].data_ptr(),
+                                   d["dtr"].data_ptr() if d["dtr"] is not None else None,
+                                   out["F"].data_ptr(), out["J"].data_ptr(),
+                                   out["pot"].data_ptr() if q else None,
+                                   out["nnb"].data_ptr(), out["list"].data_ptr(), out["ovf"].data_ptr()))
+        plan = B.nb_plan_create(ctx.h, cl, mode_id(mode))
+        try:
+            B.nb_plan_run(plan, ctx=ctx.h)
+            assert ctx.sync_status() == 0
+            for (d, out), w, q in zip(keep, ws, pot):
+                g = {k: v.cpu().numpy() for k, v in out.items() if v is not None}
+                compare(g, oracle_run(w, pot=q), w.cap, mode, pot=q)
+        finally:
+            B.nb_plan_destroy(plan)
+
+
 # ------------------------------------------------------------- host step
 
 def test_host_step_matches_oracle():
