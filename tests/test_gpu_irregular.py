@@ -49,6 +49,28 @@ def test_regular_plus_irregular_is_the_full_sum(mode):
     assert (np.abs(reg["pot"] + irr["pot"] - fP) / np.abs(fP)).max() <= ftol
 
 
+@pytest.mark.parametrize("mode", ["fp64", "mixed"])
+def test_irregular_force_with_velocity_criterion_at_an_odd_slot(mode):
+    """Lists built with the velocity criterion, the j-range at an odd slot of a
+    larger context, the potential on: the irregular sum matches the oracle's
+    irregular sum over the same neighbour sets."""
+    w = inputs.cluster(5000, 47, 48, 128, act=np.arange(1, 5000, 6, dtype=np.int32),
+                       dtr_steps=(2.0**-5, 2.0**-7))
+    off = 1001
+    with Context(w.n + off + 2) as ctx:
+        d = upload(w)
+        ctx.predict(d["x0"], d["v0"], d["a0"], d["adot0"], d["m"], d["t0"], w.t, offset=off)
+        reg = ctx.regular_force(d["act"], d["h"], w.n, dtr=d["dtr"], cap=w.cap, mode=mode, j_begin=off)
+        irr = ctx.irregular_force(d["act"], reg["nnb"], reg["list"], w.n, w.cap, mode=mode, j_begin=off, pot=True)
+        assert ctx.sync_status() == 0
+        assert not reg["ovf"].cpu().numpy().any()
+        gF, gJ = irr["F"].cpu().numpy(), irr["J"].cpu().numpy()
+    x, v = oracle_predicted(w)
+    oF, oJ = oracle.irregular(x, v, w.m, w.act, w.h, dtr=w.dtr)
+    ftol, jtol = TOL[mode]
+    assert rel_err(gF, oF).max() <= ftol and rel_err(gJ, oJ).max() <= jtol
+
+
 def test_two_float_irregular_force_on_hard_pairs_far_from_the_origin():
     """Hard pairs at separations down to 1e-5 at |x| = 1e3: the two-float
     differences keep the irregular force at the two-float tolerances, which
