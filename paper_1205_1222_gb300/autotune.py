@@ -34,7 +34,7 @@ def save(ctx, path: str, device_name: str = "") -> None:
 
 def load(ctx, path: str) -> int:
     """Insert the entries saved in `path` into `ctx`; returns how many were
-    accepted (entries whose tiling is not compiled in this build are skipped)."""
+    accepted (entries whose tiling the loaded library does not compile are skipped)."""
     h = ctx.h if hasattr(ctx, "h") else ctx
     with open(path) as f:
         doc = json.load(f)
