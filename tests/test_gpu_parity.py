@@ -131,6 +131,29 @@ def test_everyone_a_neighbour_and_overflow(cap):
         assert np.array_equal(g["list"][:, :k], o["list"][:, :k])
 
 
+@pytest.mark.parametrize("mode", ["fp64", "mixed", "fp32"])
+def test_coincident_particles_inside_the_sphere(mode):
+    """Pairs of distinct particles at exactly the same predicted position and
+    velocity (their whole start-of-step state copied) are neighbours of each
+    other: listed, kept out of the force and jerk, no NaN anywhere."""
+    import dataclasses
+    w = inputs.cluster(3000, 71, 32, 64)
+    x0, v0, a0, ad, t0 = (np.array(a) for a in (w.x0, w.v0, w.a0, w.adot0, w.t0))
+    src = np.arange(0, 3000, 97)
+    dst = (src + 500) % 3000
+    for arr in (x0, v0, a0, ad, t0):
+        arr[dst] = arr[src]
+    X, V = oracle.predict(x0, v0, a0, ad, t0, w.t)
+    h, _ = inputs.choose_radii(X, V, np.arange(w.n), 24, 40, np.random.default_rng(72))
+    w2 = dataclasses.replace(w, x0=x0, v0=v0, a0=a0, adot0=ad, t0=t0, h=h)
+    g = gpu_run(w2, mode)
+    o = oracle_run(w2)
+    assert g["status"] == 0 and np.isfinite(g["F"]).all() and np.isfinite(g["J"]).all()
+    for a, b in zip(src, dst):   # each copy is in the other's list
+        assert b in o["list"][a][:o["nnb"][a]] and a in o["list"][b][:o["nnb"][b]]
+    compare(g, o, w2.cap, mode, lists=(mode != "fp32"))
+
+
 def test_empty_active_set_launches_nothing():
     w = inputs.cluster(500, 9, 8, 16, act=np.zeros(0, dtype=np.int32))
     g = gpu_run(w, "mixed")
