@@ -488,6 +488,13 @@ def run_ours(args):
         "vs_baseline": None, "dtype": "f32" if args.mode != "fp64" else "f64", "data": "synthetic",
         "config": dict(describe(w, args.mode), parallelism=f"replicas{world}" if world > 1 else "single"),
     }
+    line["timing"] = {
+        "events": "CUDA events on the launching stream around each step; L2 flushed before each",
+        "step_ms_mean": ms, "step_ms_median": statistics.median(step_ms),
+        "force_ms_mean": fms, "force_ms_median": statistics.median(force_ms),
+        "predict_ms_mean": statistics.mean(a - b for a, b in zip(step_ms, force_ms)),
+        "step_ms_min": min(step_ms), "step_ms_max": max(step_ms),
+    }
     line["roofline"] = {
         "bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
         "traffic": profiled_traffic(r.cfg),
