@@ -413,6 +413,13 @@ def cpu_baseline(w, sample):
     base = {"value": len(rows) * w.n / dt, "unit": "interactions/s", "cores": threads, "kind": "oracle",
             "sample": f"{len(rows)} sampled active particles x all {w.n} j-particles "
                       f"({len(rows) * w.n:.3g} interactions, FP64 C, OpenMP over i, {dt:.2f} s wall)"}
+    one = rows[:max(1, len(rows) // 16)]   # the same oracle on one core, a sixteenth of the sample
+    t1 = time.perf_counter()
+    oracle.regular(x, v, w.m, w.act[one], w.h[one], cap=w.cap, threads=1)
+    d1 = time.perf_counter() - t1
+    base["single_thread"] = {"value": len(one) * w.n / d1, "cores": 1,
+                             "sample": f"{len(one)} of the sampled active particles x all {w.n} j-particles "
+                                       f"({d1:.2f} s wall)"}
     return base, o, rows
 
 
