@@ -529,7 +529,7 @@ def run_ours(args):
     if not args.no_forms:
         # the exact two-float pair form (two-float velocity differences too) beside the default
         for label, mode, cfg in (("fp64", "fp64", ""), ("fp32", "fp32", ""), ("mixed", "mixed", ""),
-                                 ("mixed_exact_pair", "mixed", "16,2,512,2")):
+                                 ("mixed_exact_pair", "mixed", "16,2,1536,14")):
             if mode == args.mode and not cfg and not args.config:
                 forms[label] = {"value": value / world, "ms_per_step": ms, "kernel_ms": fms, "tiling": r.cfg}
                 continue
@@ -714,7 +714,7 @@ def run_offset_pairs(args):
         rows = np.arange(w.n_act) if w.n_act <= 4096 else \
             np.sort(np.random.default_rng(5).choice(w.n_act, 4096, replace=False))
         o = oracle.regular(x, v, w.m, w.act[rows], w.h[rows], cap=w.cap)
-        for label, mode, cfg in (("fp32", "fp32", ""), ("mixed", "mixed", ""), ("mixed_exact_pair", "mixed", "16,2,512,2"),
+        for label, mode, cfg in (("fp32", "fp32", ""), ("mixed", "mixed", ""), ("mixed_exact_pair", "mixed", "16,2,1536,14"),
                                  ("fp64", "fp64", "")):
             r = Runner(w, mode, 0, cfg)
             if not cfg and mode != "fp64" and not args.no_tune:

@@ -59,10 +59,10 @@ enum nb_status {
 enum nb_mode {
     NB_FP64 = 0,  /* FP64 differences, FP64 pair terms, FP64 sums                   */
     NB_MIXED = 1, /* two-float (hi+lo) position differences, FP32 pair terms,         *
-                   * float-float sums per lane, FP64 across lanes and splits; the   *
-                   * default tiling (packed = 5) differences FP32-rounded velocities,*
-                   * the exact pair tiling (packed = 2) and the scalar kernels     *
-                   * two-float velocities                                           */
+                   * float-float sums per lane, across lanes and across j-splits,   *
+                   * FP64 outputs; the default tilings (packed = 5, 9) difference   *
+                   * FP32-rounded velocities, the exact pair tilings (packed = 2,   *
+                   * 14) and the scalar kernels two-float velocities               */
     NB_FP32 = 2   /* plain FP32 differences and pair terms, same sums as NB_MIXED    */
 };
 
@@ -88,8 +88,9 @@ typedef struct nb_kcfg {
                          * 5 = as 2 (two-float form only) with two-float positions and
                          * FP32 velocity differences; 5 + NL (NL >= 1) = the arithmetic
                          * of 5 (two-float form) or 2 (FP32 form) with `warps` - NL
-                         * compute warps and NL warps that build the neighbour lists.
-                         * FP64 form: 0.                                                 */
+                         * compute warps and NL warps that build the neighbour lists;
+                         * 10 + NL = the exact pair arithmetic of 2 (two-float form)
+                         * with NL list warps.  FP64 form: 0.                            */
 } nb_kcfg;
 
 /* One independent cluster of a batched call (host struct; the pointers in it

@@ -201,9 +201,8 @@ int entry_occupancy(nb_ctx *ctx, int idx, int *occ)
 }
 
 // Fill the tiling fields of one cluster descriptor.
-// Active particles per i-block of a kernel entry (the packed - 5 list warps
-// of the packed >= 6 kernels own none).
-int iblock_size(const KernelEntry &e) { return (e.packed >= 6 ? e.warps - (e.packed - 5) : e.warps) * e.ipw; }
+// Active particles per i-block of a kernel entry (its list warps own none).
+int iblock_size(const KernelEntry &e) { return (e.warps - e.lists) * e.ipw; }
 
 void tile_cluster(const KernelEntry &e, int occ, int sm, const nb_kcfg *cfg, ClusterDesc &d)
 {

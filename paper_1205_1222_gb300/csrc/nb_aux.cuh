@@ -41,9 +41,12 @@ struct KernelEntry {
     int flags;       // bit 0: velocity criterion, bit 1: potential
     int packed;      // 0: scalar kernel (nb_regf.cuh),
                      // 2: f32x2 over j-pairs on the pair-interleaved streams (nb_regf3.cuh),
-                     // 3: as 2 with two j-pairs per lane per step
+                     // 3: as 2 with two j-pairs per lane per step; 4: framed; 5: two-float
+                     // positions with FP32 velocity differences; 5 + NL / 10 + NL: the
+                     // arithmetic of 5 / 2 with NL list warps (nb_regf_ws.cuh)
     const void *fn;
     int smem;        // dynamic shared memory bytes
+    int lists = 0;   // list warps of the CTA (they own no active particles)
 };
 
 const KernelEntry *kernels_fp64(int *count);

@@ -13,6 +13,7 @@ static const KernelEntry g_mixed[] = {
     NB_KERNEL_ENTRY6(PairMixedX, 1, 12, 4, 2, 1024, 4, 1),
     NB_KERNEL_ENTRY6(PairMixedX, 1, 12, 4, 2, 1024, 4, 2),
     NB_KERNEL_ENTRY6(PairMixedX, 1, 12, 4, 2, 1024, 4, 3),
+    NB_KERNEL_ENTRY7(12, 4, 2, 1536, 2, 0),                 // exact pair form with list warps
     NB_KERNEL_ENTRY5(16, 2, 1024, 4, 0, 1),
     NB_KERNEL_ENTRY5(16, 2, 1024, 4, 1, 1),
     NB_KERNEL_ENTRY5(16, 2, 1024, 4, 2, 1),

@@ -34,7 +34,16 @@
     {                                                                                   \
         MODE, (WC) + (NL), I, JT, FL, 5 + (NL),                                         \
             reinterpret_cast<const void *>(&nb::regf3ws_kernel<FORM, WC, NL, I, JT, NST, FL>), \
-            nb::ws_smem_bytes<FORM, WC, NL, I, JT, NST>(((FL) & 2) != 0)               \
+            nb::ws_smem_bytes<FORM, WC, NL, I, JT, NST>(((FL) & 2) != 0), NL           \
+    }
+
+// The exact pair form (two-float position and velocity differences) with NL
+// list warps: packed = 10 + NL.
+#define NB_KERNEL_ENTRY7(WC, NL, I, JT, NST, FL)                                        \
+    {                                                                                   \
+        1, (WC) + (NL), I, JT, FL, 10 + (NL),                                           \
+            reinterpret_cast<const void *>(&nb::regf3ws_kernel<nb::PairMixed, WC, NL, I, JT, NST, FL>), \
+            nb::ws_smem_bytes<nb::PairMixed, WC, NL, I, JT, NST>(((FL) & 2) != 0), NL  \
     }
 
 // Framed two-float kernel (packed = 4): compact blocks of the spatially sorted
