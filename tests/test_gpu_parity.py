@@ -434,33 +434,39 @@ def test_host_step_matches_oracle():
     compare(g, oracle_run(w), w.cap, "mixed")
 
 
-def test_host_step_in_chunks_matches_the_device_call():
+@pytest.mark.parametrize("flags", [False, True])
+def test_host_step_in_chunks_matches_the_device_call(flags):
     """A large active set goes through nb_step_host in chunks (98304 active on a
     152-SM GB300: chunks of 8, 9 and 9 rounds of the persistent grid, then the
-    last, part-filled round alone),
-    each chunk's results copied back while the next computes: outputs are
-    bit-identical to one device call on the same inputs, and match the oracle
-    on sampled rows."""
+    last, part-filled round alone), each chunk's results copied back while the
+    next computes: outputs are bit-identical to one device call on the same
+    inputs, and match the oracle on sampled rows; with `flags` the call also
+    uses the velocity criterion and returns the potential."""
     import torch
-    w = inputs.cluster(100000, 19, 48, 128, act=np.arange(0, 98304, dtype=np.int32))
+    w = inputs.cluster(100000, 19, 48, 128, act=np.arange(0, 98304, dtype=np.int32),
+                       dtr_steps=(2.0**-6, 2.0**-8) if flags else None)
     pin = lambda a, dt=torch.float64: torch.as_tensor(np.ascontiguousarray(a), dtype=dt).pin_memory()
     hx = {k: pin(getattr(w, k)) for k in ("x0", "v0", "a0", "adot0", "m", "t0", "h")}
     act = pin(w.act, torch.int32)
+    dtr = pin(w.dtr) if flags else None
     F = torch.empty((w.n_act, 3), dtype=torch.float64).pin_memory()
     J = torch.empty_like(F)
+    pot = torch.empty(w.n_act, dtype=torch.float64).pin_memory() if flags else None
     nnb = torch.empty(w.n_act, dtype=torch.int32).pin_memory()
     lst = torch.zeros((w.n_act, w.cap), dtype=torch.int32).pin_memory()
     ovf = torch.empty(w.n_act, dtype=torch.uint8).pin_memory()
     with Context(w.n) as ctx:
         B.nb_step_host(ctx.h, w.n, hx["x0"], hx["v0"], hx["a0"], hx["adot0"], hx["m"], hx["t0"], w.t, w.n_act,
-                       act, hx["h"], None, w.cap, B.NB_MIXED, F, J, None, nnb, lst, ovf)
+                       act, hx["h"], dtr, w.cap, B.NB_MIXED, F, J, pot, nnb, lst, ovf)
         assert ctx.last_launches() >= 3, "prediction and at least two force launches"
-        one = gpu_run(w, "mixed", ctx=ctx)
+        one = gpu_run(w, "mixed", ctx=ctx, pot=flags)
     g = {"F": F.numpy(), "J": J.numpy(), "nnb": nnb.numpy(), "list": lst.numpy(), "ovf": ovf.numpy()}
-    for k in ("F", "J", "nnb", "list", "ovf"):
+    if flags:
+        g["pot"] = pot.numpy()
+    for k in g:
         assert np.array_equal(g[k], one[k]), k
     rows = np.sort(np.random.default_rng(3).choice(w.n_act, 256, replace=False))
-    compare(g, oracle_run(w, rows=rows), w.cap, "mixed", rows=rows)
+    compare(g, oracle_run(w, rows=rows, pot=flags), w.cap, "mixed", rows=rows, pot=flags)
 
 
 # ------------------------------------------------- device-side error paths
