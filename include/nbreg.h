@@ -219,6 +219,15 @@ void nb_plan_destroy(nb_plan *plan);
 /* Kernel launches one nb_plan_run issues (host only). */
 int nb_plan_launches(const nb_plan *plan);
 
+/* One-shot batched call: builds a plan for `clusters` (cfg = the context's
+ * configuration for `mode`), runs it on `stream`, waits for the stream and
+ * frees the plan.  Same outputs and errors as nb_plan_create followed by
+ * nb_plan_run; returns the device status like nb_sync_status.  It allocates
+ * and synchronises, so it cannot be captured: a batched step that repeats, or
+ * runs inside a CUDA graph, keeps a plan (nb_plan_capture / nb_plan_launch). */
+int nb_regular_force_batched(nb_ctx *ctx, int32_t n_clusters, const nb_cluster *clusters, int mode,
+                             nb_stream_t stream);
+
 /* One whole block step through HOST buffers: copy the j-set inputs and the
  * active set from host memory, predict (only the form `mode` needs), compute
  * the regular force, copy the results back into host memory and wait for

@@ -33,7 +33,8 @@ MODE_FORM = {NB_FP64: NB_FORM_FP64, NB_MIXED: NB_FORM_MIXED, NB_FP32: NB_FORM_FP
 EXPORTS = [
     "nb_create", "nb_destroy", "nb_predict", "nb_set_predicted", "nb_get_predicted", "nb_regular_force",
     "nb_reserve", "nb_scratch_bytes", "nb_plan_create", "nb_plan_run", "nb_plan_capture",
-    "nb_plan_launch", "nb_plan_destroy", "nb_plan_launches", "nb_step_host", "nb_sync_status",
+    "nb_plan_launch", "nb_plan_destroy", "nb_plan_launches", "nb_regular_force_batched", "nb_step_host",
+    "nb_sync_status",
     "nb_strerror", "nb_last_error", "nb_num_kernel_configs", "nb_get_kernel_config",
     "nb_set_kernel_config", "nb_get_active_config", "nb_time_regular_force", "nb_last_launches",
     "nb_sm_count", "nb_debug_set_wait", "nb_regular_force_noalloc", "nb_debug_frame_stats",
@@ -98,6 +99,7 @@ def library():
         "nb_plan_launch": ([P, P], cint),
         "nb_plan_destroy": ([P], None),
         "nb_plan_launches": ([P], cint),
+        "nb_regular_force_batched": ([P, cint, P, cint, P], cint),
         "nb_step_host": ([P, i64, P, P, P, P, P, P, dbl, i32, P, P, P, i32, cint, P, P, P, P, P, P, P], cint),
         "nb_sync_status": ([P, P], cint),
         "nb_strerror": ([cint], ctypes.c_char_p),
@@ -330,6 +332,13 @@ def nb_plan_launch(plan, stream=None, ctx=None):
 
 def nb_plan_launches(plan):
     return int(library().nb_plan_launches(plan))
+
+
+def nb_regular_force_batched(ctx, clusters, mode, stream=None):
+    """One-shot batched call (plan built, run, waited for and freed)."""
+    arr = (nb_cluster * len(clusters))(*clusters)
+    _check(ctx, library().nb_regular_force_batched(ctx, len(clusters), ctypes.cast(arr, ctypes.c_void_p), int(mode),
+                                                   _stream(stream)), "nb_regular_force_batched")
 
 
 def nb_plan_destroy(plan):

@@ -1203,6 +1203,19 @@ int nb_plan_capture(nb_plan *p, nb_stream_t stream)
     return NB_OK;
 }
 
+int nb_regular_force_batched(nb_ctx *ctx, int32_t n_clusters, const nb_cluster *clusters, int mode,
+                             nb_stream_t stream)
+{
+    nb_plan *p = nullptr;
+    int rc = nb_plan_create(ctx, n_clusters, clusters, mode, nullptr, &p);
+    if (rc != NB_OK) return rc;
+    rc = nb_plan_run(p, stream);
+    const int st = nb_sync_status(ctx, stream);   // the plan's buffers outlive its kernels
+    ctx->last_launches = rc == NB_OK ? nb_plan_launches(p) : 0;
+    nb_plan_destroy(p);
+    return rc != NB_OK ? rc : st;
+}
+
 int nb_plan_launch(nb_plan *p, nb_stream_t stream)
 {
     if (!p) return NB_ERR_ARG;

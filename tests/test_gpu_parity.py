@@ -373,6 +373,42 @@ def test_batched_plan_and_graph(mode, even):
             B.nb_plan_destroy(plan)
 
 
+@pytest.mark.parametrize("mode", ["fp64", "mixed"])
+def test_one_shot_batched_call_matches_the_plan(mode):
+    """nb_regular_force_batched (plan built, run, waited for, freed) gives the
+    outputs of an explicit plan bit for bit, and the oracle's."""
+    ws = _batch(nc=5, seed=52)
+    offs = np.cumsum([0] + [w.n + (w.n % 2) + 2 for w in ws])
+    with Context(int(offs[-1])) as ctx:
+        outs = []
+        for rep in range(2):
+            keep, cl = [], []
+            for w, off in zip(ws, offs):
+                d = upload(w)
+                if rep == 0:
+                    ctx.predict(d["x0"], d["v0"], d["a0"], d["adot0"], d["m"], d["t0"], w.t, offset=int(off))
+                out = ctx.alloc_outputs(w.n_act, w.cap)
+                keep.append((d, out))
+                cl.append(B.nb_cluster(int(off), w.n, w.n_act, w.cap, d["act"].data_ptr(), d["h"].data_ptr(),
+                                       None, out["F"].data_ptr(), out["J"].data_ptr(), None,
+                                       out["nnb"].data_ptr(), out["list"].data_ptr(), out["ovf"].data_ptr()))
+            if rep == 0:
+                B.nb_regular_force_batched(ctx.h, cl, mode_id(mode))
+                assert ctx.last_launches() >= 1
+            else:
+                plan = B.nb_plan_create(ctx.h, cl, mode_id(mode))
+                try:
+                    B.nb_plan_run(plan, ctx=ctx.h)
+                    assert ctx.sync_status() == 0
+                finally:
+                    B.nb_plan_destroy(plan)
+            outs.append([{k: v.cpu().numpy() for k, v in out.items() if v is not None} for _, out in keep])
+    for w, a, b in zip(ws, outs[0], outs[1]):
+        for k in ("F", "J", "nnb", "list", "ovf"):
+            assert np.array_equal(a[k], b[k]), k
+        compare(a, oracle_run(w), w.cap, mode)
+
+
 @pytest.mark.parametrize("mode,odd", [("mixed", False), ("mixed", True), ("fp64", True)])
 def test_batched_plan_with_mixed_flags(mode, odd):
     """A plan whose clusters differ in flags: some with the velocity criterion,
