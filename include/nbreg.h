@@ -207,7 +207,11 @@ size_t nb_scratch_bytes(nb_ctx *ctx, int64_t n_j, int32_t n_act, int32_t cap, in
  * (host array `clusters`), all in ONE persistent kernel launch plus one merge
  * launch.  A plan uploads the cluster table once and owns its scratch, so
  * nb_plan_run() allocates nothing and can be captured into a CUDA graph.
- * cfg NULL = the context's configuration for `mode`. */
+ * cfg NULL = the context's configuration for `mode`.  The paper has no
+ * counterpart (it runs one simulation per GPU); each cluster's outputs have
+ * the meaning of nb_regular_force's.  Errors: those of nb_regular_force for
+ * any cluster (NB_ERR_ARG, NB_ERR_STATE), NB_ERR_NOMEM for the plan's device
+ * memory. */
 int nb_plan_create(nb_ctx *ctx, int32_t n_clusters, const nb_cluster *clusters, int mode,
                    const nb_kcfg *cfg, nb_plan **out);
 int nb_plan_run(nb_plan *plan, nb_stream_t stream);
@@ -228,7 +232,8 @@ int nb_plan_launches(const nb_plan *plan);
 int nb_regular_force_batched(nb_ctx *ctx, int32_t n_clusters, const nb_cluster *clusters, int mode,
                              nb_stream_t stream);
 
-/* One whole block step through HOST buffers: copy the j-set inputs and the
+/* One whole block step through HOST buffers (the paper's host-side loop of
+ * prediction, GPUNB_SEND and GPUNB_REGF, Sec. 3.3 steps (iii)-(vi)): copy the j-set inputs and the
  * active set from host memory, predict (only the form `mode` needs), compute
  * the regular force, copy the results back into host memory and wait for
  * them.  All array arguments are HOST pointers (pinned memory gives
@@ -288,7 +293,8 @@ int nb_irregular_force(nb_ctx *ctx, int64_t j_begin, int64_t n_j, int32_t n_act,
                        const int32_t *nnb, const int32_t *list, int32_t cap, int mode, double *F,
                        double *J, double *pot, nb_stream_t stream);
 
-/* Autotuner.  A call's size class is (mode, flags, floor(log2 n_act),
+/* Autotuner (no counterpart in the paper, which fixes its tiling at compile
+ * time).  A call's size class is (mode, flags, floor(log2 n_act),
  * floor(log2 n_j)), flags = 1 with a velocity criterion (dtr != NULL) | 2 with
  * a potential output.  nb_autotune times, on the caller's own call (the same
  * arguments as nb_regular_force; its outputs are overwritten), every compiled
