@@ -40,6 +40,25 @@ def test_profiled_traffic_requires_the_same_tiling(tmp_path, monkeypatch):
     assert bench.profiled_traffic((16, 2, 1024, 0, 5)) is None
 
 
+def test_cpu_baseline_reports_all_cores_and_one_core():
+    """The oracle leg of the benchmark: a bounded sample timed on all host cores
+    and a sixteenth of it on one core, with the keys the benchmark line needs;
+    the sampled rows it returns are the oracle's own outputs."""
+    import numpy as np
+    import oracle
+    from paper_1205_1222_gb300 import inputs
+    w = inputs.cluster(3000, 9, 24, 64)
+    base, o, rows = bench.cpu_baseline(w, 320)
+    assert base["kind"] == "oracle" and base["unit"] == "interactions/s" and base["value"] > 0
+    assert base["cores"] >= 1 and "sample" in base
+    one = base["single_thread"]
+    assert one["cores"] == 1 and one["value"] > 0
+    assert len(rows) == 320 and np.all(np.diff(rows) > 0)
+    x, v = oracle.predict(w.x0, w.v0, w.a0, w.adot0, w.t0, w.t)
+    ref = oracle.regular(x, v, w.m, w.act[rows], w.h[rows], cap=w.cap)
+    assert np.array_equal(o["F"], ref["F"]) and np.array_equal(o["list"], ref["list"])
+
+
 def _free_port():
     s = socket.socket()
     s.bind(("127.0.0.1", 0))
