@@ -52,7 +52,9 @@ enum nb_status {
     NB_ERR_TIMEOUT = -4,     /* a bounded device wait ran out (device status)     */
     NB_ERR_STATE = -5,       /* e.g. the requested precision form was not predicted */
     NB_ERR_UNSUPPORTED = -6, /* no kernel for this combination                    */
-    NB_ERR_DEVICE_INPUT = -7 /* invalid value found on the device (index, radius) */
+    NB_ERR_DEVICE_INPUT = -7, /* invalid value found on the device (index, radius) */
+    NB_ERR_INTERNAL = -8      /* a device-side bounds check of the library's own output
+                               * indexing failed; the store was skipped (a library bug) */
 };
 
 /* Precision form of the pairwise arithmetic. */
@@ -62,12 +64,25 @@ enum nb_mode {
                    * float-float sums per lane, across lanes and across j-splits,   *
                    * FP64 outputs; the default tilings (packed = 5, 9) difference   *
                    * FP32-rounded velocities, the exact pair tilings (packed = 2,   *
-                   * 14) and the scalar kernels two-float velocities               */
+                   * 14) and the scalar kernels two-float velocities.  The float    *
+                   * forms store velocities relative to a frame velocity u (see     *
+                   * nb_predict), so an FP32 velocity difference has an absolute    *
+                   * error of about 2^-24 (|v_i - u| + |v_j - u|): at the level of  *
+                   * the pair term's other FP32 roundings as long as the predicted  *
+                   * velocities spread about u by no more than a few velocity       *
+                   * dispersions.  A cluster with any bulk velocity meets that when *
+                   * it is predicted in a call of its own (u is then its own mean   *
+                   * velocity); several clusters with different bulk velocities     *
+                   * predicted in ONE call do not, and should be predicted one call *
+                   * per cluster (or use the exact pair tilings).                   */
     NB_FP32 = 2   /* plain FP32 differences and pair terms, same sums as NB_MIXED    */
 };
 
-/* Bit mask of the predicted forms nb_predict()/nb_set_predicted() write. */
-enum nb_form_bits { NB_FORM_FP64 = 1, NB_FORM_MIXED = 2, NB_FORM_FP32 = 4, NB_FORM_ALL = 7 };
+/* Bit mask of the predicted forms nb_predict()/nb_set_predicted() write, and
+ * NB_KEEP_FRAME: store the float forms in the context's current frame
+ * velocity instead of computing a new one (see nb_predict). */
+enum nb_form_bits { NB_FORM_FP64 = 1, NB_FORM_MIXED = 2, NB_FORM_FP32 = 4, NB_FORM_ALL = 7,
+                    NB_KEEP_FRAME = 8 };
 
 typedef struct nb_ctx nb_ctx;     /* opaque, library-owned */
 typedef struct nb_plan nb_plan;   /* opaque, library-owned */
@@ -134,6 +149,19 @@ void nb_destroy(nb_ctx *ctx);
  * velocity with the mass's hi and lo parts in the w of the position pair;
  * FP32 float4 copies; the j-pair kernels' pair-interleaved copies of the
  * MIXED and FP32 forms.
+ * Velocity frame (no counterpart in the paper): the MIXED and FP32 copies
+ * hold v - u, formed in FP64 before rounding, where the frame velocity u is
+ * the mean start velocity v0 of 64 particles spread evenly over this call's
+ * range (all of them if n < 64), computed on the device inside the same
+ * launch; with NB_KEEP_FRAME in `forms` the context's current frame is used
+ * instead (the last computed one, or the one given to nb_set_frame).  Only
+ * velocity differences enter the results, so u changes no result beyond
+ * rounding; it keeps the FP32 velocity differences accurate for clusters
+ * that move through the caller's frame.  The FP64 copy holds v itself.  The
+ * context records the frame of every predicted slot range: a force call
+ * whose j-range holds slots predicted under different frames (e.g. a range
+ * predicted in two calls without NB_KEEP_FRAME on the second) returns
+ * NB_ERR_STATE instead of mixing them.
  * Errors: NB_ERR_ARG if offset < 0, n < 0, offset + n > n_max, a NULL array
  * with n > 0. */
 int nb_predict(nb_ctx *ctx, int64_t offset, int64_t n, const double *x0, const double *v0,
@@ -151,6 +179,14 @@ int nb_set_predicted(nb_ctx *ctx, int64_t offset, int64_t n, const double *x, co
  * NB_ERR_STATE if the FP64 form was not written by the last prediction. */
 int nb_get_predicted(nb_ctx *ctx, int64_t offset, int64_t n, double *x, double *v, double *m,
                      nb_stream_t stream);
+
+/* The frame velocity of later predictions with NB_KEEP_FRAME: nb_set_frame
+ * sets it from the host array u[3] (it starts a new frame, so slots predicted
+ * before keep theirs); nb_get_frame waits for the device and copies the
+ * current frame into u[3] (host).  NULL arguments: NB_ERR_ARG.  No
+ * counterpart in the paper. */
+int nb_set_frame(nb_ctx *ctx, const double *u);
+int nb_get_frame(nb_ctx *ctx, double *u);
 
 /* Regular force, jerk and neighbour list (Sec. 3.3 step (vi), criterion of
  * Sec. 3.2; ~ GPUNB_REGF).  The j-set is slots [j_begin, j_begin + n_j) of
@@ -183,12 +219,16 @@ int nb_regular_force(nb_ctx *ctx, int64_t j_begin, int64_t n_j, int32_t n_act,
  * fixed device array of 32 MiB (33554432 bytes) that every GPU loading the
  * library holds until the process exits.  A call with n_split j-splits needs
  * about n_split * n_act * (68 + 4 * cap) bytes of it (no split, no scratch).
- * Same arguments, outputs and errors as nb_regular_force, plus: a call whose
+ * Same arguments, outputs and errors as nb_regular_force, and the same tiling
+ * (the one nb_set_kernel_config chose, else the tuned one of the call's size
+ * class, else the default), so the two calls give bit-identical results; plus:
+ * a call whose
  * split scratch would exceed the array returns NB_ERR_ARG with the sizes in
  * nb_last_error (fewer active particles per call or a smaller cap fit).
  * The first call on a device looks up the array's device address; make that
  * first call before any stream capture.  All calls share the one array and it
- * keeps the last call's contents (each call clears what it needs cleared):
+ * keeps the last call's contents (nothing needs clearing: a call writes every
+ * partial it reads before reading it):
  * calls that may overlap on the GPU (other streams, other contexts on the same
  * device) race on it and must be serialised by the caller. */
 int nb_regular_force_noalloc(nb_ctx *ctx, int64_t j_begin, int64_t n_j, int32_t n_act,
@@ -249,7 +289,7 @@ int nb_step_host(nb_ctx *ctx, int64_t n, const double *x0, const double *v0, con
                  int32_t *list, uint8_t *ovf, nb_stream_t stream);
 
 /* Wait for `stream`, then read and clear the device status word.  Returns
- * NB_OK, NB_ERR_TIMEOUT, NB_ERR_DEVICE_INPUT or NB_ERR_CUDA. */
+ * NB_OK, NB_ERR_INTERNAL, NB_ERR_TIMEOUT, NB_ERR_DEVICE_INPUT or NB_ERR_CUDA. */
 int nb_sync_status(nb_ctx *ctx, nb_stream_t stream);
 
 /* Text for a status code (static storage). */

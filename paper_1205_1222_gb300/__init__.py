@@ -11,10 +11,10 @@ from __future__ import annotations
 
 from . import binding as _b
 from .binding import (MODES, NB_FORM_ALL, NB_FORM_FP32, NB_FORM_FP64, NB_FORM_MIXED, NB_FP32,
-                      NB_FP64, NB_MIXED, NbError, nb_kcfg)
+                      NB_FP64, NB_KEEP_FRAME, NB_MIXED, NbError, nb_kcfg)
 
 __all__ = ["Context", "NbError", "MODES", "NB_FP64", "NB_MIXED", "NB_FP32", "NB_FORM_ALL",
-           "NB_FORM_FP64", "NB_FORM_MIXED", "NB_FORM_FP32", "nb_kcfg", "mode_id"]
+           "NB_FORM_FP64", "NB_FORM_MIXED", "NB_FORM_FP32", "NB_KEEP_FRAME", "nb_kcfg", "mode_id"]
 
 
 def mode_id(mode) -> int:

@@ -23,10 +23,12 @@ NB_ERR_TIMEOUT = -4
 NB_ERR_STATE = -5
 NB_ERR_UNSUPPORTED = -6
 NB_ERR_DEVICE_INPUT = -7
+NB_ERR_INTERNAL = -8
 
 NB_FP64, NB_MIXED, NB_FP32 = 0, 1, 2
 MODES = {"fp64": NB_FP64, "mixed": NB_MIXED, "fp32": NB_FP32}
 NB_FORM_FP64, NB_FORM_MIXED, NB_FORM_FP32, NB_FORM_ALL = 1, 2, 4, 7
+NB_KEEP_FRAME = 8
 MODE_FORM = {NB_FP64: NB_FORM_FP64, NB_MIXED: NB_FORM_MIXED, NB_FP32: NB_FORM_FP32}
 
 # Exported symbols declared in include/nbreg.h (checked by the ABI test).
@@ -39,6 +41,7 @@ EXPORTS = [
     "nb_set_kernel_config", "nb_get_active_config", "nb_time_regular_force", "nb_last_launches",
     "nb_sm_count", "nb_debug_set_wait", "nb_regular_force_noalloc", "nb_debug_frame_stats",
     "nb_autotune", "nb_num_tuned", "nb_get_tuned", "nb_set_tuned", "nb_irregular_force",
+    "nb_set_frame", "nb_get_frame",
 ]
 
 
@@ -121,6 +124,8 @@ def library():
         "nb_irregular_force": ([P, i64, i64, i32, P, P, P, i32, cint, P, P, P, P], cint),
         "nb_get_tuned": ([P, cint, ctypes.POINTER(nb_tuned)], cint),
         "nb_set_tuned": ([P, ctypes.POINTER(nb_tuned)], cint),
+        "nb_set_frame": ([P, ctypes.POINTER(dbl)], cint),
+        "nb_get_frame": ([P, ctypes.POINTER(dbl)], cint),
     }
     for name, (args, res) in sig.items():
         f = getattr(lib, name)
@@ -189,6 +194,17 @@ def nb_set_predicted(ctx, offset, n, x, v, m, forms=0, stream=None):
 def nb_get_predicted(ctx, offset, n, x, v, m=None, stream=None):
     _check(ctx, library().nb_get_predicted(ctx, int(offset), int(n), _p(x), _p(v), _p(m), _stream(stream)),
            "nb_get_predicted")
+
+
+def nb_set_frame(ctx, u):
+    a = (ctypes.c_double * 3)(*[float(x) for x in u])
+    _check(ctx, library().nb_set_frame(ctx, a), "nb_set_frame")
+
+
+def nb_get_frame(ctx):
+    a = (ctypes.c_double * 3)()
+    _check(ctx, library().nb_get_frame(ctx, a), "nb_get_frame")
+    return [a[0], a[1], a[2]]
 
 
 def nb_regular_force(ctx, j_begin, n_j, n_act, act, h, dtr, cap, mode, F, J, pot, nnb, lst, ovf,

@@ -80,6 +80,13 @@ struct nb_ctx {
     float4 *pif[4] = {};   // pair-interleaved FP32 streams
     int forms_valid = 0;
     int *d_status = nullptr;
+    double *d_frame = nullptr;   // [3] frame velocity of the float forms (device)
+    // Frame under which each predicted slot range holds its float forms:
+    // begin -> (end, frame epoch), disjoint ranges.  Every prediction that
+    // computes a new frame starts a new epoch; NB_KEEP_FRAME and nb_set_frame
+    // keep / start one explicitly.
+    std::map<int64_t, std::pair<int64_t, uint64_t>> frames;
+    uint64_t epoch = 0, epochs = 0;
     void *scratch = nullptr;
     size_t scratch_bytes = 0;
     nb_kcfg cfg[3];
@@ -314,6 +321,53 @@ int grow_scratch(nb_ctx *ctx, size_t need, cudaStream_t st)
     return NB_OK;
 }
 
+// Record that slots [a, b) now hold float forms predicted in frame epoch e.
+void note_frame(nb_ctx *ctx, int64_t a, int64_t b, uint64_t e)
+{
+    if (a >= b) return;
+    auto &f = ctx->frames;
+    auto it = f.lower_bound(a);
+    if (it != f.begin()) {
+        auto pr = std::prev(it);
+        if (pr->second.first > a) {   // a range that starts before a and reaches into [a, b)
+            const auto tail = pr->second;
+            pr->second.first = a;
+            if (tail.first > b) f[b] = tail;
+        }
+    }
+    it = f.lower_bound(a);
+    while (it != f.end() && it->first < b) {
+        const auto cur = *it;
+        it = f.erase(it);
+        if (cur.second.first > b) { f[b] = cur.second; break; }
+    }
+    f[a] = {b, e};
+}
+
+// A call's float-form arithmetic differences velocities stored relative to a
+// frame velocity: every slot of its j-range must share one frame.
+int check_frames(nb_ctx *ctx, int mode, int64_t a, int64_t n)
+{
+    if (mode == NB_FP64 || n <= 0) return NB_OK;
+    const int64_t b = a + n;
+    auto &f = ctx->frames;
+    auto it = f.upper_bound(a);
+    if (it != f.begin()) --it;
+    bool seen = false;
+    uint64_t e = 0;
+    for (; it != f.end() && it->first < b; ++it) {
+        if (it->second.first <= a) continue;
+        if (seen && it->second.second != e) {
+            ctx->err = "the j-range holds slots predicted in different velocity frames (predict it in one call, "
+                       "or pass NB_KEEP_FRAME to the later predictions)";
+            return NB_ERR_STATE;
+        }
+        seen = true;
+        e = it->second.second;
+    }
+    return NB_OK;
+}
+
 struct Call {
     int64_t j_begin, n_j;
     int32_t n_act;
@@ -344,7 +398,7 @@ int check_call(nb_ctx *ctx, const Call &c)
         ctx->err = "the requested form has not been predicted";
         return NB_ERR_STATE;
     }
-    return NB_OK;
+    return check_frames(ctx, c.mode, c.j_begin, c.n_j);
 }
 
 ClusterDesc make_desc(const Call &c)
@@ -463,6 +517,7 @@ int run_single(nb_ctx *ctx, const Call &c, const nb_kcfg *cfg_override, cudaStre
         mp.n_clusters = 1;
         mp.n_total = d.n_act;
         mp.ff = c.mode != NB_FP64;
+        mp.status = ctx->d_status;
         nb::launch_merge(mp, st);
         NB_CUDA(ctx, cudaGetLastError());
         ctx->last_launches = 2 + sort_launches;
@@ -485,6 +540,7 @@ const char *nb_strerror(int s)
     case NB_ERR_STATE: return "invalid state (form not predicted, or scratch too small under capture)";
     case NB_ERR_UNSUPPORTED: return "unsupported configuration";
     case NB_ERR_DEVICE_INPUT: return "invalid active index or radius found on the device";
+    case NB_ERR_INTERNAL: return "a device-side bounds check of the library's own indexing failed";
     default: return "unknown status";
     }
 }
@@ -525,6 +581,8 @@ int nb_create(nb_ctx **out, int device, int64_t n_max)
     for (int k = 0; k < 4; k++) alloc(reinterpret_cast<void **>(&c->pif[k]), npairs * sizeof(float4));
     alloc(reinterpret_cast<void **>(&c->d_status), sizeof(int));
     if (rc == NB_OK && cudaMemset(c->d_status, 0, sizeof(int)) != cudaSuccess) rc = NB_ERR_CUDA;
+    alloc(reinterpret_cast<void **>(&c->d_frame), 4 * sizeof(double));
+    if (rc == NB_OK && cudaMemset(c->d_frame, 0, 4 * sizeof(double)) != cudaSuccess) rc = NB_ERR_CUDA;
     if (rc == NB_OK && cudaDeviceGetAttribute(&c->sm_count, cudaDevAttrMultiProcessorCount, device) != cudaSuccess)
         rc = NB_ERR_CUDA;
     if (rc != NB_OK) {
@@ -541,7 +599,7 @@ void nb_destroy(nb_ctx *c)
     DeviceGuard guard(c->device);
     cudaDeviceSynchronize();
     void *bufs[] = {c->pos64, c->vel64, c->mx_hi, c->mx_lo, c->mv_hi, c->mv_lo, c->pos32, c->vel32,
-                    c->d_status, c->scratch, c->stage, c->sort};
+                    c->d_status, c->d_frame, c->scratch, c->stage, c->sort};
     for (void *b : bufs)
         if (b) cudaFree(b);
     for (float4 *b : c->pim)
@@ -564,6 +622,8 @@ static int predict_impl(nb_ctx *ctx, int64_t offset, int64_t n, const double *x0
     if (!ctx) return NB_ERR_ARG;
     if (offset < 0 || n < 0 || offset + n > ctx->n_max) { ctx->err = "slots outside the context"; return NB_ERR_ARG; }
     if (n > 0 && (!x0 || !v0 || !m || (a0 && (!adot0 || !t0)))) { ctx->err = "NULL array"; return NB_ERR_ARG; }
+    const bool keep = (forms & NB_KEEP_FRAME) != 0;
+    forms &= ~NB_KEEP_FRAME;
     if (forms == 0) forms = NB_FORM_ALL;
     if (forms & ~NB_FORM_ALL) { ctx->err = "bad forms mask"; return NB_ERR_ARG; }
     DeviceGuard guard(ctx->device);
@@ -572,6 +632,8 @@ static int predict_impl(nb_ctx *ctx, int64_t offset, int64_t n, const double *x0
     p.n = n;
     p.x0 = x0; p.v0 = v0; p.a0 = a0; p.adot0 = adot0; p.m = m; p.t0 = t0; p.t = t;
     p.forms = forms;
+    p.keep_frame = keep ? 1 : 0;
+    p.frame = ctx->d_frame;
     p.pos64 = ctx->pos64; p.vel64 = ctx->vel64;
     p.mx_hi = ctx->mx_hi; p.mx_lo = ctx->mx_lo; p.mv_hi = ctx->mv_hi; p.mv_lo = ctx->mv_lo;
     p.pos32 = ctx->pos32; p.vel32 = ctx->vel32;
@@ -580,6 +642,10 @@ static int predict_impl(nb_ctx *ctx, int64_t offset, int64_t n, const double *x0
     nb::launch_predict(p, st);
     NB_CUDA(ctx, cudaGetLastError());
     ctx->forms_valid = forms;   // forms not rewritten are stale now
+    if (n > 0) {
+        if (!keep) ctx->epoch = ++ctx->epochs;
+        note_frame(ctx, offset, offset + n, ctx->epoch);
+    }
     return NB_OK;
 }
 
@@ -619,6 +685,24 @@ int nb_get_predicted(nb_ctx *ctx, int64_t offset, int64_t n, double *x, double *
     if (m)
         NB_CUDA(ctx, cudaMemcpy2DAsync(m, sizeof(double), p + 3 * sizeof(double), w, sizeof(double), n,
                                        cudaMemcpyDeviceToDevice, st));
+    return NB_OK;
+}
+
+int nb_set_frame(nb_ctx *ctx, const double *u)
+{
+    if (!ctx || !u) return NB_ERR_ARG;
+    DeviceGuard guard(ctx->device);
+    NB_CUDA(ctx, cudaMemcpy(ctx->d_frame, u, 3 * sizeof(double), cudaMemcpyHostToDevice));
+    ctx->epoch = ++ctx->epochs;
+    return NB_OK;
+}
+
+int nb_get_frame(nb_ctx *ctx, double *u)
+{
+    if (!ctx || !u) return NB_ERR_ARG;
+    DeviceGuard guard(ctx->device);
+    NB_CUDA(ctx, cudaDeviceSynchronize());
+    NB_CUDA(ctx, cudaMemcpy(u, ctx->d_frame, 3 * sizeof(double), cudaMemcpyDeviceToHost));
     return NB_OK;
 }
 
@@ -667,6 +751,10 @@ int nb_sync_status(nb_ctx *ctx, nb_stream_t stream)
     int h = 0;
     NB_CUDA(ctx, cudaMemcpy(&h, ctx->d_status, sizeof(int), cudaMemcpyDeviceToHost));
     if (h != 0) NB_CUDA(ctx, cudaMemset(ctx->d_status, 0, sizeof(int)));
+    if (h & nb::DEV_BOUNDS) {
+        ctx->err = "a bounds check of the library's own output indexing failed on the device (store skipped)";
+        return NB_ERR_INTERNAL;
+    }
     if (h & nb::DEV_TIMEOUT) { ctx->err = "a bounded copy wait ran out on the device"; return NB_ERR_TIMEOUT; }
     if (h & nb::DEV_BAD_INPUT) { ctx->err = "invalid active index or radius on the device"; return NB_ERR_DEVICE_INPUT; }
     return NB_OK;
@@ -762,6 +850,8 @@ int nb_irregular_force(nb_ctx *ctx, int64_t j_begin, int64_t n_j, int32_t n_act,
         ctx->err = "the requested form has not been predicted";
         return NB_ERR_STATE;
     }
+    const int frc = check_frames(ctx, mode, j_begin, n_j);
+    if (frc != NB_OK) return frc;
     DeviceGuard guard(ctx->device);
     nb::IrrParams p{};
     p.j_begin = j_begin;
@@ -1178,6 +1268,7 @@ int nb_plan_run(nb_plan *p, nb_stream_t stream)
         mp.n_clusters = p->n_merge;
         mp.n_total = p->merge_total;
         mp.ff = p->mode != NB_FP64;
+        mp.status = ctx->d_status;
         nb::launch_merge(mp, st);
         NB_CUDA(ctx, cudaGetLastError());
     }
@@ -1304,8 +1395,10 @@ extern "C" int nb_regular_force_noalloc(nb_ctx *ctx, int64_t j_begin, int64_t n_
     void *scratch = nullptr;
     rc = noalloc_scratch(ctx, &scratch);
     if (rc != NB_OK) return rc;
-    const nb_kcfg cfg = ctx->cfg_set[c.mode] ? ctx->cfg[c.mode] : default_cfg(c.mode);
+    // the tiling nb_regular_force would take: set by nb_set_kernel_config, else
+    // the tuned one of the call's size class, else the default
     const int flags = (c.dtr ? 1 : 0) | (c.pot ? 2 : 0);
+    const nb_kcfg cfg = pick_cfg(ctx, c.mode, flags, c.n_act, c.n_j);
     int idx = find_entry(c.mode, cfg, flags);
     if (idx < 0) { ctx->err = "no kernel for this mode"; return NB_ERR_UNSUPPORTED; }
     if (registry().all[idx].packed >= 2 && (c.j_begin & 1)) idx = layout_fallback(c.mode, idx, flags);
@@ -1327,13 +1420,10 @@ extern "C" int nb_regular_force_noalloc(nb_ctx *ctx, int64_t j_begin, int64_t n_
                    " (use fewer active particles or a smaller cap per call, or nb_regular_force)";
         return NB_ERR_ARG;
     }
+    // The array keeps the previous call's contents.  Nothing needs clearing:
+    // every work item stores (does not add to) its own (split, particle)
+    // partials, count and list slots, and the merge reads only those.
     carve_scratch(d, static_cast<char *>(scratch));
-    if (d.n_split > 1) {
-        // The array keeps the previous call's contents: the partial sums and
-        // counts every split starts from are cleared (pF and pcnt are contiguous).
-        const char *end = reinterpret_cast<const char *>(d.pcnt + static_cast<size_t>(d.n_split) * d.n_act);
-        NB_CUDA(ctx, cudaMemsetAsync(d.pF, 0, static_cast<size_t>(end - reinterpret_cast<const char *>(d.pF)), st));
-    }
 
     nb::RegfParams p{};
     p.js = tile_streams(ctx, c.mode, e);
@@ -1354,6 +1444,7 @@ extern "C" int nb_regular_force_noalloc(nb_ctx *ctx, int64_t j_begin, int64_t n_
         mp.n_clusters = 1;
         mp.n_total = d.n_act;
         mp.ff = c.mode != NB_FP64;
+        mp.status = ctx->d_status;
         nb::launch_merge(mp, st);
         NB_CUDA(ctx, cudaGetLastError());
         ctx->last_launches = 2;

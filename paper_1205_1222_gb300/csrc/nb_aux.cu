@@ -7,7 +7,14 @@
 //    two-float float4 hi/lo pairs of position and velocity (mass in the
 //    hi-position w), and plain FP32 float4 copies; the two float forms are
 //    also written pair-interleaved (float4 k of j-pair P holds components of
-//    slots 2P and 2P+1) for the j-pair packed kernels.
+//    slots 2P and 2P+1) for the j-pair packed kernels.  The float forms hold
+//    velocities relative to a frame velocity u (v - u formed in FP64, then
+//    rounded), so that an FP32 velocity difference v_j - v_i, which rounds
+//    |v_i - u| + |v_j - u| rather than |v_i| + |v_j|, is as accurate for a
+//    cluster moving through the caller's frame as for one at rest in it.  u is
+//    the mean start velocity of kFrameSamples particles spread evenly over the
+//    call's range (every block computes the same value, in the same order, so
+//    no launch or grid-wide step is added), or the context's stored frame.
 //  * merge_kernel: one warp per active particle of a cluster whose j-range
 //    was split over several work items; sums the per-split partial force,
 //    jerk and potential in a fixed order (float-float pairs for the float
@@ -53,8 +60,47 @@ __device__ __forceinline__ void write_pairs(float4 *const *streams, const float 
 
 }  // namespace
 
+// Particles sampled for the frame velocity of a prediction.
+constexpr int kFrameSamples = 64;
+
+// Frame velocity of this call: the plain mean of the start velocities of
+// particles floor(k n / S), k = 0 .. S-1 (S = min(n, kFrameSamples)), summed
+// in FP32 in a fixed order (a lane tree per warp, then the warps in order),
+// so every block gets the same bits.  Any velocity near the cluster's bulk
+// motion serves; the mean of a sample is one within about a dispersion / 8.
+// All threads of the block must call it.
+__device__ void frame_velocity(const PredParams &p, double (&u)[3])
+{
+    __shared__ float part[32][3];
+    if (p.keep_frame) {
+        for (int c = 0; c < 3; c++) u[c] = p.frame[c];
+        return;
+    }
+    const int64_t S = p.n < kFrameSamples ? p.n : kFrameSamples;
+    float s[3] = {0.f, 0.f, 0.f};
+    for (int64_t k = threadIdx.x; k < S; k += blockDim.x) {
+        const int64_t j = k * p.n / S;
+        for (int c = 0; c < 3; c++) s[c] += __double2float_rn(p.v0[3 * j + c]);
+    }
+    for (int o = 16; o > 0; o >>= 1)
+        for (int c = 0; c < 3; c++) s[c] += __shfl_xor_sync(0xffffffffu, s[c], o);
+    const int warp = threadIdx.x >> 5, nw = (blockDim.x + 31) >> 5;
+    if ((threadIdx.x & 31) == 0)
+        for (int c = 0; c < 3; c++) part[warp][c] = s[c];
+    __syncthreads();
+    for (int c = 0; c < 3; c++) {
+        float t = 0.f;
+        for (int w = 0; w < nw; w++) t += part[w][c];
+        u[c] = S > 0 ? static_cast<double>(t / static_cast<float>(S)) : 0.0;
+    }
+    if (blockIdx.x == 0 && threadIdx.x == 0)
+        for (int c = 0; c < 3; c++) p.frame[c] = u[c];
+}
+
 __global__ void predict_kernel(const PredParams p)
 {
+    double u[3];
+    frame_velocity(p, u);   // before any thread leaves: it holds a block barrier
     const int64_t j = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
     // every lane takes part in the shuffles; lanes past the end only pass values along
     const bool live = j < p.n;
@@ -86,13 +132,15 @@ __global__ void predict_kernel(const PredParams p)
     // left as it is (a later prediction of that slot fills it).
     const bool even = (s & 1) == 0;
     const bool partner_in = ((threadIdx.x & 31) + 1 < 32) && (j + 1 < p.n);
+    double vr[3];   // velocity in the frame of the float forms
+    for (int k = 0; k < 3; k++) vr[k] = v[k] - u[k];
     if (p.forms & 2) {
         float xh[3], xl[3], vh[3], vl[3];
         for (int k = 0; k < 3; k++) {
             xh[k] = __double2float_rn(x[k]);
             xl[k] = __double2float_rn(x[k] - static_cast<double>(xh[k]));
-            vh[k] = __double2float_rn(v[k]);
-            vl[k] = __double2float_rn(v[k] - static_cast<double>(vh[k]));
+            vh[k] = __double2float_rn(vr[k]);
+            vl[k] = __double2float_rn(vr[k] - static_cast<double>(vh[k]));
         }
         const float mh = __double2float_rn(m);
         const float ml = __double2float_rn(m - static_cast<double>(mh));
@@ -108,8 +156,8 @@ __global__ void predict_kernel(const PredParams p)
     }
     if (p.forms & 4) {
         const float vals[8] = {__double2float_rn(x[0]), __double2float_rn(x[1]), __double2float_rn(x[2]),
-                               __double2float_rn(m), __double2float_rn(v[0]), __double2float_rn(v[1]),
-                               __double2float_rn(v[2]), 0.f};
+                               __double2float_rn(m), __double2float_rn(vr[0]), __double2float_rn(vr[1]),
+                               __double2float_rn(vr[2]), 0.f};
         if (live) {
             p.pos32[s] = make_float4(vals[0], vals[1], vals[2], vals[3]);
             p.vel32[s] = make_float4(vals[4], vals[5], vals[6], 0.f);
@@ -178,7 +226,13 @@ __global__ void merge_kernel(const MergeParams p)
                 if (ex <= e) src += step;
             }
             const int off = e - __shfl_sync(0xffffffffu, excl, src);
-            if (e < ncopy) to[e] = d.plist[(static_cast<int64_t>(s0 + src) * na + i) * d.cap + off];
+            // off < min(count of split src, cap) and s0 + src < S by construction
+            if (e < ncopy) {
+                if (off >= 0 && off < d.cap && s0 + src < S)
+                    to[e] = d.plist[(static_cast<int64_t>(s0 + src) * na + i) * d.cap + off];
+                else
+                    atomicOr(p.status, DEV_BOUNDS);
+            }
         }
         running += total;
     }

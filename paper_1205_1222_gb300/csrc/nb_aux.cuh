@@ -14,6 +14,12 @@ struct PredParams {
     const double *x0, *v0, *a0, *adot0, *m, *t0;   // a0 == nullptr: copy x0, v0 unchanged
     double t;
     int forms;
+    // Frame velocity u of the float forms (their velocities are stored as
+    // v - u): keep_frame != 0 reads it from frame; otherwise every block
+    // computes the same u from a sample of this call's start velocities and
+    // block 0 stores it to frame.
+    int keep_frame;
+    double *frame;     // [3], context-owned device memory
     double4_32a *pos64, *vel64;
     float4 *mx_hi, *mx_lo, *mv_hi, *mv_lo;
     float4 *pos32, *vel32;
@@ -29,6 +35,7 @@ struct MergeParams {
     int32_t n_clusters;            // merged clusters
     int64_t n_total;               // total merged active particles (one warp each)
     int ff;                        // 1: split slots hold float-float pairs (float forms), 0: doubles (FP64 form)
+    int *status;                   // device status word (DEV_BOUNDS if a list read would leave its row)
 };
 
 void launch_predict(const PredParams &p, cudaStream_t st);

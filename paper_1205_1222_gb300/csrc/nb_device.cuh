@@ -14,6 +14,7 @@ struct FrameRec;   // nb_sort.cuh
 enum : int {
     DEV_TIMEOUT = 1,    // a bounded wait on a copy ran out
     DEV_BAD_INPUT = 2,  // an active index or a radius was invalid
+    DEV_BOUNDS = 4,     // a bounds check of the library's own output indexing failed
 };
 
 // Predicted j-set of one precision form: base pointers of its streams.
@@ -195,8 +196,23 @@ __device__ __forceinline__ void ff_keep(FFKeep<I> &k, int q, int c, float hi, fl
     if ((threadIdx.x & 31) == (slot & 31)) { k.h[slot >> 5] = hi; k.l[slot >> 5] = lo; }
 }
 
+// Bounds check of the end-of-item stores: output row i (-1 = no particle,
+// skipped silently) of j-split sp.  Every stored index is in range by
+// construction (rows come from positions < n_act of the active set, splits
+// from the item number); a failure records DEV_BOUNDS in the status word and
+// the store is skipped, so an indexing bug surfaces as a status, not as a
+// stray write.
+__device__ __forceinline__ bool row_ok(const ClusterDesc &d, int sp, int64_t i, int *status)
+{
+    if (i < 0) return false;
+    if (i < d.n_act && sp >= 0 && sp < d.n_split) return true;
+    atomicOr(status, DEV_BOUNDS);
+    return false;
+}
+
 template <int I, int NC>
-__device__ __forceinline__ void write_item_ff(const ClusterDesc &d, int sp, const FFKeep<I> &k, const int (&oi)[I])
+__device__ __forceinline__ void write_item_ff(const ClusterDesc &d, int sp, const FFKeep<I> &k, const int (&oi)[I],
+                                              int *status)
 {
     static_assert(NC <= 7, "F, J and the potential");
     const int lane = threadIdx.x & 31;
@@ -208,7 +224,7 @@ __device__ __forceinline__ void write_item_ff(const ClusterDesc &d, int sp, cons
 #pragma unroll
         for (int qq = 4 * r; qq < I && qq < 4 * r + 4; qq++)
             if (qq == q) i = oi[qq];
-        if (q >= I || i < 0 || c >= 7) continue;
+        if (q >= I || c >= 7 || !row_ok(d, sp, i, status)) continue;
         const int64_t ii = i;
         const float h = c < NC ? k.h[r] : 0.f, l = c < NC ? k.l[r] : 0.f;
         if (d.n_split == 1) {

@@ -431,7 +431,7 @@ __global__ void __launch_bounds__(W * 32) regf_kernel(const RegfParams p)
                 out[6] = acc[k].p;
                 for (int o = 16; o > 0; o >>= 1)
                     for (int c = 0; c < 7; c++) out[c] += __shfl_xor_sync(0xffffffffu, out[c], o);
-                if (lane == 0 && idx[k] >= 0) {
+                if (lane == 0 && row_ok(d, sp, idx[k], p.status)) {
                     const int64_t i = idx[k];
                     if (d.n_split == 1) {
                         for (int c = 0; c < 3; c++) { d.F[3 * i + c] = out[c]; d.J[3 * i + c] = out[3 + c]; }
@@ -464,11 +464,11 @@ __global__ void __launch_bounds__(W * 32) regf_kernel(const RegfParams p)
 #pragma unroll
                 for (int c = 0; c < NC; c++) ff_keep(kept, k, c, hi[c], lo[c]);
             }
-            write_item_ff<I, NC>(d, sp, kept, idx);
+            write_item_ff<I, NC>(d, sp, kept, idx, p.status);
         }
 #pragma unroll
         for (int k = 0; k < I; k++) {
-            if (lane == 0 && idx[k] >= 0) {
+            if (lane == 0 && row_ok(d, sp, idx[k], p.status)) {
                 const int64_t i = idx[k];
                 if (d.n_split == 1) {
                     d.nnb[i] = cnt[k];

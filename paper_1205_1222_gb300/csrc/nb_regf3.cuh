@@ -611,11 +611,11 @@ __global__ void __launch_bounds__(W * 32, MINB) regf3_kernel(const RegfParams p)
                 ff_keep(kept, q, c, hi, lo);
             }
         }
-        write_item_ff<I, NC>(d, sp, kept, oidx);
+        write_item_ff<I, NC>(d, sp, kept, oidx, p.status);
 #pragma unroll
         for (int q = 0; q < I; q++) {
             const int64_t i = oidx[q];
-            if (lane == 0 && i >= 0) {
+            if (lane == 0 && row_ok(d, sp, i, p.status)) {
                 const int nq = cnt[q];
                 if (d.n_split == 1) {
                     d.nnb[i] = nq;

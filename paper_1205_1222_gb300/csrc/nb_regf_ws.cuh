@@ -234,7 +234,7 @@ __global__ void __launch_bounds__((WC + NL) * 32, 1) regf3ws_kernel(const RegfPa
                     out[c] = static_cast<double>(hi) + static_cast<double>(lo);
                 }
                 const int64_t i = oidx[q];
-                if (lane == 0 && i >= 0) {
+                if (lane == 0 && row_ok(d, sp, i, p.status)) {
                     if (d.n_split == 1) {
                         for (int c = 0; c < 3; c++) { d.F[3 * i + c] = out[c]; d.J[3 * i + c] = out[3 + c]; }
                         if (POT && d.pot) d.pot[i] = out[6];
@@ -336,7 +336,7 @@ __global__ void __launch_bounds__((WC + NL) * 32, 1) regf3ws_kernel(const RegfPa
 #pragma unroll
                     for (int q = 0; q < I; q++) {
                         const int64_t i = oidx[c][q];
-                        if (i < 0) continue;
+                        if (!row_ok(d, sp, i, p.status)) continue;
                         if (d.n_split == 1) {
                             d.nnb[i] = cnt[c][q];
                             d.ovf[i] = cnt[c][q] > d.cap ? 1 : 0;

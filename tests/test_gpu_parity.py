@@ -226,6 +226,53 @@ def test_random_sweep(c):
     compare(g, oracle_run(w, cap=c["cap"], pot=c["pot"]), c["cap"], c["mode"], pot=c["pot"])
 
 
+def _block_edge_cases():
+    # (tiling, i-block size): list-warp kernels own 12 x 2 = 24 particles per
+    # CTA block, the 16-warp j-pair kernels 32
+    tilings = [((16, 2, 1024, 0, 9), 24), ((16, 2, 1536, 0, 14), 24), ((16, 2, 512, 0, 5), 32),
+               ((16, 2, 512, 0, 2), 32)]
+    out = []
+    for t, ib in tilings:
+        for n_act in (1, ib - 1, ib + 1, 37 * ib + 1, 152 * ib + 1):
+            for split in (0, 2):
+                out.append((t, n_act, split))
+    return out
+
+
+@pytest.mark.parametrize("tiling,n_act,split", _block_edge_cases(),
+                         ids=lambda v: "-".join(map(str, v)) if isinstance(v, tuple) else str(v))
+def test_last_i_block_part_filled(tiling, n_act, split):
+    """The last CTA block of active particles holds one particle (n_act = 1
+    mod the i-block), or is one short of full, with and without j-splits
+    (split = 2: two 512/1024/1536-j tiles per work item): the end-of-item
+    stores and the split merge must write exactly rows 0 .. n_act-1, and a
+    full grid round plus one particle (152 blocks + 1) must wrap to the next
+    round."""
+    import torch
+    n = 6000
+    w = inputs.cluster(n, 4100 + n_act, 40, 64,
+                       act=np.sort(np.random.default_rng(n_act).choice(n, n_act, replace=False)))
+    cfg = B.nb_kcfg(tiling[0], tiling[1], tiling[2], split, tiling[4])
+    with Context(n) as ctx:
+        d = upload(w)
+        ctx.predict(d["x0"], d["v0"], d["a0"], d["adot0"], d["m"], d["t0"], w.t)
+        ctx.set_config("mixed", cfg)
+        # outputs with a guard row past the end that must stay untouched
+        out = ctx.alloc_outputs(n_act + 1, w.cap)
+        for k in ("F", "J"):
+            out[k].fill_(7.0)
+        out["nnb"].fill_(-9); out["ovf"].fill_(5)
+        view = {k: (v[:n_act] if v is not None else None) for k, v in out.items()}
+        ctx.regular_force(d["act"], d["h"], w.n, cap=w.cap, mode="mixed", out=view)
+        assert ctx.sync_status() == 0
+        if split:
+            assert ctx.last_launches() == 2
+        g = {k: v.cpu().numpy() for k, v in out.items() if v is not None}
+    assert np.all(g["F"][n_act] == 7.0) and np.all(g["J"][n_act] == 7.0)
+    assert g["nnb"][n_act] == -9 and g["ovf"][n_act] == 5 and np.all(g["list"][n_act] == -1)
+    compare({k: v[:n_act] for k, v in g.items()}, oracle_run(w), w.cap, "mixed")
+
+
 def test_split_and_unsplit_paths_agree():
     w = inputs.cluster(20000, 14, 64, 256, act=np.arange(0, 20000, 97, dtype=np.int32))
     o = oracle_run(w)
@@ -580,16 +627,28 @@ def test_config3_kroupa_131072_active_2048(cfg3, mode):
     compare(g, oracle_run(w), w.cap, mode)
 
 
-def test_config3_all_active_sampled(cfg3):
-    """The benchmark's workload (N = n_act = 131072, mixed form, default
-    configuration): 1024 sampled particles against the oracle one by one, and
-    every particle's count equal to the count its radius was built for."""
+@pytest.fixture(scope="module")
+def cfg3_oracle(cfg3):
+    """The oracle on every row of the benchmark's workload (1.7e10 FP64
+    interactions, OpenMP over all host cores)."""
+    return oracle_run(cfg3)
+
+
+@pytest.mark.parametrize("tiling", [None, (16, 2, 1536, 0, 14)], ids=["default", "exact_pair"])
+def test_config3_all_active_every_row(cfg3, cfg3_oracle, tiling):
+    """The benchmark's workload (N = n_act = 131072, two-float form) in the
+    launch configuration the benchmark times (the default tiling, which the
+    autotuner also picks at this size) and in the exact pair form: every one
+    of the 131072 rows against the oracle, element by element (force, jerk,
+    count, overflow flag and every list entry), and every particle's count
+    equal to the count its radius was built for."""
     w = cfg3
-    g = gpu_run(w, "mixed")
+    g = gpu_run(w, "mixed", cfg=None if tiling is None else B.nb_kcfg(*tiling))
     assert g["status"] == 0
     assert np.array_equal(g["nnb"], w.meta["K"])
-    rows = np.sort(np.random.default_rng(33).choice(w.n_act, 1024, replace=False))
-    eF, eJ = compare(g, oracle_run(w, rows=rows), w.cap, "mixed", rows=rows)
+    eF, eJ = compare(g, cfg3_oracle, w.cap, "mixed")
+    print(f"all {w.n_act} rows: force max {eF.max():.2e} rms {np.sqrt((eF ** 2).mean()):.2e}, "
+          f"jerk max {eJ.max():.2e} rms {np.sqrt((eJ ** 2).mean()):.2e}")
 
 
 @pytest.fixture(scope="module")
@@ -648,15 +707,83 @@ def test_default_mixed_kernel_is_two_float_positions(cfg2):
     compare(g, oracle_run(cfg2), cfg2.cap, "mixed")
 
 
-@pytest.mark.parametrize("bulk", [1.0, 4.0])
+# velocity dispersion (1D) of the Henon-unit Plummer sphere: sqrt(1/6)
+SIGMA = 6.0 ** -0.5
+
+
+@pytest.mark.parametrize("bulk", [1.0, 4.0, 100.0])
 def test_two_float_positions_with_bulk_velocity(bulk):
-    """FP32 velocity differences round u (|v_i| + |v_j|): a bulk velocity of a
-    few times the dispersion (~0.7 in these units) still meets the two-float
-    tolerances; the exact pair form (packed = 2) does at any bulk velocity."""
+    """A cluster moving at `bulk` velocity dispersions through the caller's
+    frame: the predictor stores the float forms' velocities relative to the
+    cluster's own frame velocity, so the FP32 velocity differences of the
+    default kernels (packed 5 and, with list warps, 9) meet the two-float
+    tolerances with exact lists at 100 dispersions as at rest; so does the
+    exact pair form (packed = 2)."""
     u = np.array([1.0, -0.5, 0.25])
-    w = inputs.cluster(8192, 37, 64, 256, bulk_v=bulk * u / np.linalg.norm(u))
+    w = inputs.cluster(8192, 37, 64, 256, bulk_v=bulk * SIGMA * u / np.linalg.norm(u))
     o = oracle_run(w)
-    for packed in (5, 2):
-        g = gpu_run(w, "mixed", cfg=B.nb_kcfg(16, 2, 512, 0, packed))
+    for cfg in (B.nb_kcfg(16, 2, 512, 0, 5), B.nb_kcfg(16, 2, 512, 0, 2), None):   # None: the default (9)
+        g = gpu_run(w, "mixed", cfg=cfg)
         assert g["status"] == 0
         compare(g, o, w.cap, "mixed")
+
+
+def test_frame_velocity_is_the_sampled_mean_and_matters():
+    """The frame velocity is the mean start velocity of 64 particles spread
+    evenly over the predicted range; predicting the same moving cluster with
+    a zero frame instead (nb_set_frame + NB_KEEP_FRAME: FP32 velocities in the
+    caller's frame, as without the frame) loses the jerk tolerance of the
+    default form at 100 dispersions, so the test above does depend on the
+    frame."""
+    u = np.array([1.0, -0.5, 0.25])
+    bulk = 100.0 * SIGMA * u / np.linalg.norm(u)
+    w = inputs.cluster(8192, 37, 64, 256, bulk_v=bulk)
+    o = oracle_run(w)
+    with Context(w.n) as ctx:
+        d = upload(w)
+        ctx.predict(d["x0"], d["v0"], d["a0"], d["adot0"], d["m"], d["t0"], w.t)
+        k = (np.arange(64) * w.n) // 64
+        want = w.v0[k].astype(np.float32).astype(np.float64).mean(axis=0)
+        got = np.array(B.nb_get_frame(ctx.h))
+        assert np.allclose(got, want, rtol=0, atol=1e-4), (got, want)
+        g_frame = gpu_run(w, "mixed", ctx=ctx)
+        B.nb_set_frame(ctx.h, [0.0, 0.0, 0.0])
+        g_zero = gpu_run(w, "mixed", ctx=ctx, forms=B.NB_FORM_MIXED | B.NB_KEEP_FRAME)
+        assert B.nb_get_frame(ctx.h) == [0.0, 0.0, 0.0]
+    eJ_frame = rel_err(g_frame["J"], o["J"]).max()
+    eJ_zero = rel_err(g_zero["J"], o["J"]).max()
+    print(f"jerk error at 100 dispersions: frame {eJ_frame:.2e}, zero frame {eJ_zero:.2e}")
+    assert eJ_frame <= TOL["mixed"][1] < eJ_zero
+
+
+def test_a_range_predicted_under_two_frames_is_refused():
+    """Two halves of one cluster predicted in separate calls each get their
+    own frame; a force call over both halves is refused (NB_ERR_STATE) rather
+    than mixing them.  With NB_KEEP_FRAME on the second call the halves share
+    the first call's frame and the call matches the oracle."""
+    import torch
+    w = inputs.cluster(4000, 38, 32, 64, bulk_v=[3.0, 0.0, 0.0])
+    o = oracle_run(w)
+    half = w.n // 2
+    with Context(w.n) as ctx:
+        d = upload(w)
+        sl = lambda k, a, b: d[k][a:b]
+        for keep in (0, B.NB_KEEP_FRAME):
+            ctx.predict(*(sl(k, 0, half) for k in ("x0", "v0", "a0", "adot0", "m", "t0")), w.t, offset=0)
+            ctx.predict(*(sl(k, half, w.n) for k in ("x0", "v0", "a0", "adot0", "m", "t0")), w.t, offset=half,
+                        forms=keep)
+            if not keep:
+                with pytest.raises(B.NbError) as e:
+                    ctx.regular_force(d["act"], d["h"], w.n, cap=w.cap, mode="mixed")
+                assert e.value.status == B.NB_ERR_STATE and "frame" in str(e.value)
+                # the FP64 form holds velocities in the caller's frame and is unaffected
+                g64 = ctx.regular_force(d["act"], d["h"], w.n, cap=w.cap, mode="fp64")
+                assert ctx.sync_status() == 0
+                compare({k: v.cpu().numpy() for k, v in g64.items() if v is not None}, o, w.cap, "fp64")
+                # a call inside one half is fine
+                ctx.regular_force(d["act"][:10], d["h"][:10], half, cap=w.cap, mode="mixed")
+                assert ctx.sync_status() == 0
+            else:
+                g = ctx.regular_force(d["act"], d["h"], w.n, cap=w.cap, mode="mixed")
+                assert ctx.sync_status() == 0
+                compare({k: v.cpu().numpy() for k, v in g.items() if v is not None}, o, w.cap, "mixed")

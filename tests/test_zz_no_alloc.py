@@ -6,7 +6,9 @@ memory belongs to another allocator) use this call: its split partials live in
 a fixed device array instead of scratch grown with cudaMalloc.  The test runs
 a case whose j-range is split (so the fixed array is used), through the C-ABI,
 twice in a row, and compares each result with nb_regular_force on the same
-inputs, within the tolerances of the other parity tests.  It builds its own
+inputs: both calls take the same tiling (also after a tuned tiling is loaded
+for the call's size class), so the results must agree bit for bit, and they
+must meet the oracle tolerances of the other parity tests.  It builds its own
 inputs and context, so it passes alone in a fresh process or after the rest of
 the suite; the file name makes pytest collect it last.
 """
@@ -38,6 +40,11 @@ def _call(fn, ctx, d, w, mode, cap):
     return {k: v.cpu().numpy() for k, v in out.items() if v is not None}, launches
 
 
+def _same(got, ref):
+    for k in ("F", "J", "nnb", "list", "ovf"):
+        assert np.array_equal(got[k], ref[k]), k
+
+
 @pytest.mark.parametrize("mode", ["mixed", "fp64"])
 def test_noalloc_matches_regular_force_twice(workload, mode):
     w = workload
@@ -49,7 +56,33 @@ def test_noalloc_matches_regular_force_twice(workload, mode):
         for _ in range(2):
             got, launches = _call(B.nb_regular_force_noalloc, ctx, d, w, mode, w.cap)
             assert launches == 2
+            _same(got, ref)
             compare(got, ref, w.cap, mode)
+
+
+def test_noalloc_takes_the_tuned_tiling(workload):
+    """With a tuned entry loaded for the call's size class (a 512-j tiling
+    split into 8 parts instead of the default), both calls run that tiling:
+    bit-identical results, and the default tiling's results differ in the
+    last bits (the summation order changed)."""
+    w = workload
+    with Context(w.n) as ctx:
+        d = upload(w)
+        ctx.predict(d["x0"], d["v0"], d["a0"], d["adot0"], d["m"], d["t0"], w.t)
+        default, _ = _call(B.nb_regular_force, ctx, d, w, "mixed", w.cap)
+        t = B.nb_tuned()
+        t.mode, t.flags = B.NB_MIXED, 0
+        t.act_class, t.j_class = int(np.log2(w.n_act)), int(np.log2(w.n))
+        t.cfg = B.nb_kcfg(16, 2, 512, 4, 5)
+        B.nb_set_tuned(ctx.h, t)
+        ref, ref_launches = _call(B.nb_regular_force, ctx, d, w, "mixed", w.cap)
+        assert ref_launches == 2
+        assert not np.array_equal(ref["J"], default["J"]), "the tuned tiling was not taken"
+        for _ in range(2):
+            got, launches = _call(B.nb_regular_force_noalloc, ctx, d, w, "mixed", w.cap)
+            assert launches == 2
+            _same(got, ref)
+        compare(ref, default, w.cap, "mixed")
 
 
 def test_noalloc_rejects_a_call_beyond_its_fixed_scratch(workload):
