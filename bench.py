@@ -55,13 +55,15 @@ def parse_args():
     ap.add_argument("--config", default="", help="kernel tiling warps,ipw,jtile,packed[,split] "
                                                  "(default: the autotuner's choice)")
     ap.add_argument("--no-tune", action="store_true", help="skip the autotuner (library default tiling)")
-    ap.add_argument("--workload", default="headline", choices=["headline", "batched64", "offset-pairs", "velocity", "irregular", "blockstep"],
+    ap.add_argument("--workload", default="headline", choices=["headline", "batched64", "offset-pairs", "velocity", "irregular", "blockstep",
+                                                      "needed"],
                     help="headline: the benchmark line; batched64: 64 independent clusters, one persistent "
                          "launch in a CUDA graph vs one launch per cluster; offset-pairs: N=262144 offset "
                          "cluster with 10%% hard pairs, FP32 vs two-float vs FP64 with errors; velocity: the "
                          "headline workload with the velocity neighbour criterion; irregular: the irregular "
                          "force over the lists of the headline workload; blockstep: N=16384 with active "
-                         "subsets of 16..16384, two-float (autotuned) and FP64 forms")
+                         "subsets of 16..16384, two-float (autotuned) and FP64 forms; needed: all-j vs "
+                         "needed-only prediction for the irregular force on the same subsets")
     ap.add_argument("--n", type=int, default=131072,
                     help="j-particles (131072 = the benchmark workload; smaller N builds the same kind of "
                          "cluster, used for profiling captures)")
@@ -670,13 +672,24 @@ def run_batched(args):
                 f = [int(x) for x in args.config.split(",")]
                 pcfg = B.nb_kcfg(f[0], f[1], f[2], f[4] if len(f) > 4 else 0, f[3])
             plan = B.nb_plan_create(ctx.h, cl, mode, pcfg)
+            tuned = None
             try:
+                if pcfg is None and not args.no_tune:
+                    t0 = time.perf_counter()
+                    best, best_ms = B.nb_plan_autotune(plan, reps=2, stream=stream, ctx=ctx.h)
+                    tuned = {"chosen": list(best.as_tuple()), "best_ms": best_ms,
+                             "seconds": time.perf_counter() - t0,
+                             "note": "native nb_plan_autotune over every compiled tiling x j-split length on the "
+                                     "plan's own clusters, before the timed region"}
+                plan_cfg = list(B.nb_plan_get_config(plan).as_tuple())
                 B.nb_plan_capture(plan, stream=stream, ctx=ctx.h)
                 for _ in range(max(args.warmup, 3)):
                     predict(); B.nb_plan_launch(plan, stream=stream, ctx=ctx.h)
                 graph_ms = _timed_events(lambda: (predict(), B.nb_plan_launch(plan, stream=stream, ctx=ctx.h)),
                                          args.steps, flush, stream, torch)
                 plan_launches = 1 + B.nb_plan_launches(plan)
+                stream.synchronize()
+                graph_out = [{k: v.cpu().numpy() for k, v in out.items() if v is not None} for _, _, out in keep]
             finally:
                 B.nb_plan_destroy(plan)
 
@@ -688,8 +701,23 @@ def run_batched(args):
             for _ in range(max(args.warmup, 3)):
                 per_cluster()
             loop_ms = _timed_events(per_cluster, args.steps, flush, stream, torch)
+            stream.synchronize()
+            loop_out = [{k: v.cpu().numpy() for k, v in out.items() if v is not None} for _, _, out in keep]
         st = ctx.sync_status(stream)
     g, l = statistics.mean(graph_ms), statistics.mean(loop_ms)
+    # correctness of the timed outputs: lists of the graph-replayed plan equal
+    # to the per-cluster calls', and every row of every cluster against the
+    # oracle (FP64, all host cores)
+    import oracle
+    mism = sum(int(np.any(a[k] != b[k])) for a, b in zip(graph_out, loop_out) for k in ("nnb", "list", "ovf"))
+    eFs, eJs, bad = [], [], 0
+    t0 = time.perf_counter()
+    for w, go in zip(ws, graph_out):
+        x, v = oracle.predict(w.x0, w.v0, w.a0, w.adot0, w.t0, w.t)
+        o = oracle.regular(x, v, w.m, w.act, w.h, cap=w.cap)
+        acc = accuracy(go, o, np.arange(w.n_act), w.cap)
+        eFs.append(acc["F_max"]); eJs.append(acc["J_max"]); bad += acc["list_mismatches"]
+    oracle_s = time.perf_counter() - t0
     print(json.dumps({
         "metric": "regular-force interactions/s, 64 independent clusters, one persistent launch in a CUDA graph",
         "value": inter / (g / 1e3), "unit": "interactions/s", "n_gpus": 1, "steps": args.steps,
@@ -703,7 +731,10 @@ def run_batched(args):
         "per_cluster_launches": {"value": inter / (l / 1e3), "ms_per_step": l,
                                  "launches_per_step": 1 + len(ws)},
         "graph_launches_per_step": plan_launches, "speedup_vs_per_cluster": l / g,
-        "plan_tiling": args.config or "default",
+        "plan_tiling": plan_cfg, "autotune": tuned,
+        "accuracy_vs_oracle": {"rows": "every row of every cluster", "F_max": max(eFs), "J_max": max(eJs),
+                               "list_mismatches": bad, "oracle_seconds": oracle_s},
+        "graph_vs_per_cluster_list_mismatches": mism,
     }), flush=True)
 
 
@@ -891,6 +922,98 @@ def run_blockstep(args):
     }), flush=True)
 
 
+def _graph_us(fn, device, reps=20):
+    """Device time per call of `reps` calls of fn(stream) captured in one CUDA
+    graph and replayed (L2 warm, no host launches); best of 3 replays."""
+    import torch
+    side = torch.cuda.Stream(device)
+    side.wait_stream(torch.cuda.current_stream(device))
+    with torch.cuda.stream(side):
+        fn(side)
+        torch.cuda.synchronize(device)
+        g = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(g, stream=side):
+            for _ in range(reps):
+                fn(side)
+    g.replay()
+    torch.cuda.synchronize(device)
+    best = float("inf")
+    for _ in range(3):
+        a = torch.cuda.Event(enable_timing=True)
+        b = torch.cuda.Event(enable_timing=True)
+        a.record(); g.replay(); b.record()
+        torch.cuda.synchronize(device)
+        best = min(best, a.elapsed_time(b) * 1e3 / reps)
+    return best
+
+
+def run_needed(args):
+    """Needed-only prediction (Sec. 3.5, the NPACT switch) on the N = 16384
+    cluster and on the N = 131072 Kroupa cluster: for active subsets of 16 ..
+    4096, the prediction that the irregular force needs (all j; only the
+    active particles and their listed neighbours; the library's switch
+    between the two) plus the irregular force, graph-replayed per step; the
+    irregular results of the needed-only and full predictions are compared
+    bit for bit."""
+    import numpy as np
+    import torch
+
+    import oracle
+    from paper_1205_1222_gb300 import Context, binding as B, build, inputs
+    build.build()
+    torch.cuda.set_device(0)
+    dv = lambda a, dt=torch.float64: torch.as_tensor(np.ascontiguousarray(a), dtype=dt, device="cuda")
+    out_sets = []
+    for label, full in (("N=16384 equal-mass Plummer, seed 2", inputs.cached(inputs.config2)),
+                        ("N=131072 Kroupa Plummer, seed 3", inputs.cached(inputs.config3))):
+        x, v = oracle.predict(full.x0, full.v0, full.a0, full.adot0, full.t0, full.t)
+        d = {k: dv(getattr(full, k)) for k in ("x0", "v0", "a0", "adot0", "m", "t0")}
+        res = []
+        for n_act in (16, 64, 256, 1024, 4096):
+            w = inputs.subset(full, n_act, 2)
+            o = oracle.regular(x, v, w.m, w.act, w.h, cap=w.cap)
+            act, nnb, lst = dv(w.act, torch.int32), dv(o["nnb"], torch.int32), dv(o["list"], torch.int32)
+            named = np.zeros(full.n, dtype=bool)
+            named[w.act] = True
+            for k in range(n_act):
+                named[o["list"][k, :min(o["nnb"][k], w.cap)]] = True
+            row = {"n_act": n_act, "named_slots": int(named.sum()), "list_entries": int(o["nnb"].sum())}
+            with Context(full.n) as ctx:
+                ctx.predict(d["x0"], d["v0"], d["a0"], d["adot0"], d["m"], d["t0"], full.t, forms=B.NB_FORM_MIXED)
+
+                def pred_all(st):
+                    B.nb_predict(ctx.h, 0, full.n, d["x0"], d["v0"], d["a0"], d["adot0"], d["m"], d["t0"], full.t,
+                                 B.NB_FORM_MIXED | B.NB_KEEP_FRAME, st)
+
+                def pred_needed(st, only=True):
+                    B.nb_predict_needed(ctx.h, 0, full.n, n_act, act, nnb, lst, w.cap, d["x0"], d["v0"], d["a0"],
+                                        d["adot0"], d["m"], d["t0"], full.t,
+                                        B.NB_FORM_MIXED | (B.NB_NEEDED_ONLY if only else 0), st)
+                outs = {}
+
+                def irr(st, key):
+                    outs[key] = ctx.irregular_force(act, nnb, lst, full.n, w.cap, mode="mixed", stream=st)
+                row["predict_all_us"] = _graph_us(pred_all, 0)
+                row["predict_needed_us"] = _graph_us(pred_needed, 0)
+                row["predict_switch_us"] = _graph_us(lambda st: pred_needed(st, only=False), 0)
+                row["all_plus_irregular_us"] = _graph_us(lambda st: (pred_all(st), irr(st, "all")), 0)
+                row["needed_plus_irregular_us"] = _graph_us(lambda st: (pred_needed(st), irr(st, "needed")), 0)
+                torch.cuda.synchronize()
+                row["status"] = ctx.sync_status()
+                row["bit_identical"] = bool(torch.equal(outs["all"]["F"], outs["needed"]["F"]) and
+                                            torch.equal(outs["all"]["J"], outs["needed"]["J"]))
+            res.append(row)
+        cross = next((r["n_act"] for r in res if r["predict_needed_us"] >= r["predict_all_us"]), None)
+        out_sets.append({"workload": label, "N": full.n, "sizes": res, "needed_slower_from_n_act": cross})
+    print(json.dumps({
+        "metric": "prediction time per block step for the irregular force: all j vs needed-only",
+        "unit": "us", "n_gpus": 1, "dtype": "f64 polynomial, two-float stored form", "data": "synthetic",
+        "config": {"workload": "random active subsets, ~64 / ~100 neighbours, cap 256",
+                   "timing": "20 calls replayed from one CUDA graph, best of 3, L2 warm"},
+        "sets": out_sets,
+    }), flush=True)
+
+
 def main():
     args = parse_args()
     if args.impl == "reference":
@@ -905,6 +1028,8 @@ def main():
         run_irregular(args)
     elif args.workload == "blockstep":
         run_blockstep(args)
+    elif args.workload == "needed":
+        run_needed(args)
     else:
         run_ours(args)
 

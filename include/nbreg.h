@@ -80,9 +80,10 @@ enum nb_mode {
 
 /* Bit mask of the predicted forms nb_predict()/nb_set_predicted() write, and
  * NB_KEEP_FRAME: store the float forms in the context's current frame
- * velocity instead of computing a new one (see nb_predict). */
+ * velocity instead of computing a new one (see nb_predict); NB_NEEDED_ONLY:
+ * nb_predict_needed predicts only the slots it names (see there). */
 enum nb_form_bits { NB_FORM_FP64 = 1, NB_FORM_MIXED = 2, NB_FORM_FP32 = 4, NB_FORM_ALL = 7,
-                    NB_KEEP_FRAME = 8 };
+                    NB_KEEP_FRAME = 8, NB_NEEDED_ONLY = 16 };
 
 typedef struct nb_ctx nb_ctx;     /* opaque, library-owned */
 typedef struct nb_plan nb_plan;   /* opaque, library-owned */
@@ -168,6 +169,36 @@ int nb_predict(nb_ctx *ctx, int64_t offset, int64_t n, const double *x0, const d
                const double *a0, const double *adot0, const double *m, const double *t0,
                double t, int forms, nb_stream_t stream);
 
+/* Needed-only prediction (Sec. 3.5: when few particles are needed the
+ * paper's host library predicts only those, the NPACT switch between
+ * GPUIRR_PRED_ACT and GPUIRR_PRED_ALL of Appendix C).  Predicts, with the
+ * polynomial and stored forms of nb_predict, the slots of the range
+ * [offset, offset + n) that an irregular-force call with the same act, nnb,
+ * list and cap reads: act[k] and the first min(nnb[k], cap) entries of list
+ * row k, for k < n_act.  One launch of one thread per (active particle, list
+ * slot); a slot named several times is predicted by each thread naming it,
+ * with identical results.  The input arrays are those of the whole range
+ * ([n][3], [n], indexed like act).  The switch: the call predicts the whole
+ * range instead (nb_predict with NB_KEEP_FRAME) when that is the cheaper
+ * launch by a time model measured on GB300, i.e. when
+ * 4.3 us + 0.075 ns * n_act * (cap + 1) >= 2.06 us + 0.108 ns * n (at n =
+ * 16384 always; at n = 131072 with cap 256 from about 620 active particles);
+ * NB_NEEDED_ONLY in `forms` turns the switch off, and then the slots it does
+ * not name keep their values.  It uses the
+ * context's current velocity frame, so every slot of the range must have been
+ * predicted in that frame (NB_ERR_STATE otherwise: predict the range in full
+ * first).  forms (0 = the forms valid now) must be forms the last prediction
+ * wrote (NB_ERR_STATE otherwise); afterwards only those are valid.  Not a step
+ * of the regular force, which needs every j-particle predicted.  An index
+ * outside [0, n) or a negative count is skipped and reported as
+ * NB_ERR_DEVICE_INPUT by nb_sync_status.  Holds no state between calls (it can
+ * be captured in a CUDA graph).  Errors: NB_ERR_ARG for a range outside the
+ * context, negative sizes or NULL arrays. */
+int nb_predict_needed(nb_ctx *ctx, int64_t offset, int64_t n, int32_t n_act, const int32_t *act,
+                      const int32_t *nnb, const int32_t *list, int32_t cap, const double *x0,
+                      const double *v0, const double *a0, const double *adot0, const double *m,
+                      const double *t0, double t, int forms, nb_stream_t stream);
+
 /* Store already-predicted positions x, velocities v ([n][3]) and masses m
  * ([n]) in slots [offset, offset + n) (the bare GPUNB_SEND of the paper).
  * Same errors as nb_predict. */
@@ -247,7 +278,9 @@ size_t nb_scratch_bytes(nb_ctx *ctx, int64_t n_j, int32_t n_act, int32_t cap, in
  * (host array `clusters`), all in ONE persistent kernel launch plus one merge
  * launch.  A plan uploads the cluster table once and owns its scratch, so
  * nb_plan_run() allocates nothing and can be captured into a CUDA graph.
- * cfg NULL = the context's configuration for `mode`.  The paper has no
+ * cfg NULL = the tiling nb_plan_autotune recorded for the plan's batched size
+ * class, else the context's configuration for a single call of the summed
+ * size (see nb_autotune).  The paper has no
  * counterpart (it runs one simulation per GPU); each cluster's outputs have
  * the meaning of nb_regular_force's.  Errors: those of nb_regular_force for
  * any cluster (NB_ERR_ARG, NB_ERR_STATE), NB_ERR_NOMEM for the plan's device
@@ -262,6 +295,21 @@ int nb_plan_launch(nb_plan *plan, nb_stream_t stream);
 void nb_plan_destroy(nb_plan *plan);
 /* Kernel launches one nb_plan_run issues (host only). */
 int nb_plan_launches(const nb_plan *plan);
+/* The tiling the plan runs (split = j-tiles per j-split of every cluster, 0 =
+ * the plan's heuristic).  Host only. */
+int nb_plan_get_config(const nb_plan *plan, nb_kcfg *out);
+/* Autotuner of a plan (no counterpart in the paper): times nb_plan_run of the
+ * plan's own cluster table, `reps` runs after one warm-up (CUDA events on
+ * `stream`; the clusters' outputs are overwritten), for every compiled tiling
+ * of the plan's mode with its flags, each with the plan's j-split heuristic
+ * and with fixed j-split lengths of 1, 2, 4, ... tiles up to the largest
+ * cluster's tile count; rebuilds the plan with the fastest (a graph captured
+ * from the plan is dropped: capture again) and records it in the context's
+ * tuned table under the batched size class (mode, flags | 4, floor(log2 of the
+ * summed n_act), floor(log2 of the largest n_j)), which later nb_plan_create
+ * calls with cfg NULL use.  *best / *best_ms (either may be NULL) receive the
+ * winner and its mean time per run.  Allocates, synchronises; not capturable. */
+int nb_plan_autotune(nb_plan *plan, int reps, nb_stream_t stream, nb_kcfg *best, float *best_ms);
 
 /* One-shot batched call: builds a plan for `clusters` (cfg = the context's
  * configuration for `mode`), runs it on `stream`, waits for the stream and

@@ -29,6 +29,7 @@ NB_FP64, NB_MIXED, NB_FP32 = 0, 1, 2
 MODES = {"fp64": NB_FP64, "mixed": NB_MIXED, "fp32": NB_FP32}
 NB_FORM_FP64, NB_FORM_MIXED, NB_FORM_FP32, NB_FORM_ALL = 1, 2, 4, 7
 NB_KEEP_FRAME = 8
+NB_NEEDED_ONLY = 16
 MODE_FORM = {NB_FP64: NB_FORM_FP64, NB_MIXED: NB_FORM_MIXED, NB_FP32: NB_FORM_FP32}
 
 # Exported symbols declared in include/nbreg.h (checked by the ABI test).
@@ -41,7 +42,7 @@ EXPORTS = [
     "nb_set_kernel_config", "nb_get_active_config", "nb_time_regular_force", "nb_last_launches",
     "nb_sm_count", "nb_debug_set_wait", "nb_regular_force_noalloc", "nb_debug_frame_stats",
     "nb_autotune", "nb_num_tuned", "nb_get_tuned", "nb_set_tuned", "nb_irregular_force",
-    "nb_set_frame", "nb_get_frame",
+    "nb_set_frame", "nb_get_frame", "nb_predict_needed", "nb_plan_autotune", "nb_plan_get_config",
 ]
 
 
@@ -125,6 +126,9 @@ def library():
         "nb_get_tuned": ([P, cint, ctypes.POINTER(nb_tuned)], cint),
         "nb_set_tuned": ([P, ctypes.POINTER(nb_tuned)], cint),
         "nb_set_frame": ([P, ctypes.POINTER(dbl)], cint),
+        "nb_plan_autotune": ([P, cint, P, ctypes.POINTER(nb_kcfg), ctypes.POINTER(ctypes.c_float)], cint),
+        "nb_plan_get_config": ([P, ctypes.POINTER(nb_kcfg)], cint),
+        "nb_predict_needed": ([P, i64, i64, i32, P, P, P, i32, P, P, P, P, P, P, dbl, cint, P], cint),
         "nb_get_frame": ([P, ctypes.POINTER(dbl)], cint),
     }
     for name, (args, res) in sig.items():
@@ -194,6 +198,13 @@ def nb_set_predicted(ctx, offset, n, x, v, m, forms=0, stream=None):
 def nb_get_predicted(ctx, offset, n, x, v, m=None, stream=None):
     _check(ctx, library().nb_get_predicted(ctx, int(offset), int(n), _p(x), _p(v), _p(m), _stream(stream)),
            "nb_get_predicted")
+
+
+def nb_predict_needed(ctx, offset, n, n_act, act, nnb, lst, cap, x0, v0, a0, adot0, m, t0, t, forms=0,
+                      stream=None):
+    _check(ctx, library().nb_predict_needed(ctx, int(offset), int(n), int(n_act), _p(act), _p(nnb), _p(lst),
+                                            int(cap), _p(x0), _p(v0), _p(a0), _p(adot0), _p(m), _p(t0), float(t),
+                                            int(forms), _stream(stream)), "nb_predict_needed")
 
 
 def nb_set_frame(ctx, u):
@@ -348,6 +359,21 @@ def nb_plan_launch(plan, stream=None, ctx=None):
 
 def nb_plan_launches(plan):
     return int(library().nb_plan_launches(plan))
+
+
+def nb_plan_get_config(plan):
+    c = nb_kcfg()
+    _check(None, library().nb_plan_get_config(plan, ctypes.byref(c)), "nb_plan_get_config")
+    return c
+
+
+def nb_plan_autotune(plan, reps=3, stream=None, ctx=None):
+    """Tune the plan's tiling on its own clusters; returns (best nb_kcfg, mean ms per run)."""
+    best = nb_kcfg()
+    ms = ctypes.c_float()
+    _check(ctx, library().nb_plan_autotune(plan, int(reps), _stream(stream), ctypes.byref(best), ctypes.byref(ms)),
+           "nb_plan_autotune")
+    return best, float(ms.value)
 
 
 def nb_regular_force_batched(ctx, clusters, mode, stream=None):

@@ -124,6 +124,10 @@ struct nb_plan {
     void *scratch = nullptr;
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t exec = nullptr;
+    std::vector<nb_cluster> clusters;   // the caller's cluster table (for re-tiling by the autotuner)
+    nb_kcfg cfg{};                      // the tiling the plan runs (split: tiles per j-split, 0 = heuristic)
+    int flags = 0;                      // union of the clusters' flags
+    int64_t act_sum = 0, j_max = 0;
 };
 
 namespace {
@@ -162,6 +166,10 @@ uint64_t tune_key(int mode, int flags, int act_class, int j_class)
     return static_cast<uint64_t>(mode) | static_cast<uint64_t>(flags) << 4 |
            static_cast<uint64_t>(act_class) << 8 | static_cast<uint64_t>(j_class) << 16;
 }
+
+// Flag bit of the tuned table's batched classes (plans), beside the velocity
+// criterion (1) and potential (2) bits of a call.
+constexpr int kBatchedClass = 4;
 
 // Tiling of a call: the one chosen with nb_set_kernel_config, else the tuned
 // one of the call's size class, else the mode's default.
@@ -688,6 +696,78 @@ int nb_get_predicted(nb_ctx *ctx, int64_t offset, int64_t n, double *x, double *
     return NB_OK;
 }
 
+// The switch between needed-only and full prediction, from graph-replayed
+// times on GB300 (two-float stored form): a full prediction of n slots takes
+// about 2.06 us + 0.108 ns per slot (3.8 us at n = 16384, 16.2 us at 131072);
+// a needed-only one about 4.3 us + 0.15 ns per list entry, and lists hold
+// about half of their cap slots, i.e. ~0.075 ns per (active particle, list
+// slot) thread.
+static bool needed_not_worth_it(int64_t n, int32_t n_act, int32_t cap)
+{
+    const double threads = static_cast<double>(n_act) * (static_cast<double>(cap) + 1.0);
+    return 4300.0 + 0.075 * threads >= 2060.0 + 0.108 * static_cast<double>(n);
+}
+
+int nb_predict_needed(nb_ctx *ctx, int64_t offset, int64_t n, int32_t n_act, const int32_t *act,
+                      const int32_t *nnb, const int32_t *list, int32_t cap, const double *x0, const double *v0,
+                      const double *a0, const double *adot0, const double *m, const double *t0, double t,
+                      int forms, nb_stream_t stream)
+{
+    if (!ctx) return NB_ERR_ARG;
+    if (offset < 0 || n < 0 || offset + n > ctx->n_max) { ctx->err = "slots outside the context"; return NB_ERR_ARG; }
+    if (n_act < 0 || cap < 0) { ctx->err = "negative n_act or cap"; return NB_ERR_ARG; }
+    if (n_act > 0 && n == 0) { ctx->err = "active particles with an empty range"; return NB_ERR_ARG; }
+    if (n_act > 0 && (!act || !nnb || (cap > 0 && !list) || !x0 || !v0 || !a0 || !adot0 || !m || !t0)) {
+        ctx->err = "NULL array";
+        return NB_ERR_ARG;
+    }
+    const bool only = (forms & NB_NEEDED_ONLY) != 0;
+    forms &= ~(NB_KEEP_FRAME | NB_NEEDED_ONLY);   // always the current frame
+    if (forms == 0) forms = ctx->forms_valid;
+    if (forms & ~NB_FORM_ALL) { ctx->err = "bad forms mask"; return NB_ERR_ARG; }
+    if (forms == 0 || (forms & ~ctx->forms_valid)) {
+        ctx->err = "needed-only prediction of a form the range's last prediction did not write";
+        return NB_ERR_STATE;
+    }
+    // the slots it does not rewrite must already be in the current frame
+    for (auto it = ctx->frames.begin(); it != ctx->frames.end(); ++it)
+        if (it->first < offset + n && it->second.first > offset && it->second.second != ctx->epoch) {
+            ctx->err = "the range was predicted in another velocity frame than the current one (predict it in "
+                       "full, or set the frame, first)";
+            return NB_ERR_STATE;
+        }
+    if (n_act == 0) return NB_OK;
+    if (!only && needed_not_worth_it(n, n_act, cap))   // the NPACT switch: predict the whole range
+        return predict_impl(ctx, offset, n, x0, v0, a0, adot0, m, t0, t, forms | NB_KEEP_FRAME,
+                            static_cast<cudaStream_t>(stream));
+    DeviceGuard guard(ctx->device);
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    nb::NeededParams np{};
+    nb::PredParams &p = np.pp;
+    p.offset = offset;
+    p.n = n;
+    p.x0 = x0; p.v0 = v0; p.a0 = a0; p.adot0 = adot0; p.m = m; p.t0 = t0; p.t = t;
+    p.forms = forms;
+    p.keep_frame = 1;
+    p.frame = ctx->d_frame;
+    p.pos64 = ctx->pos64; p.vel64 = ctx->vel64;
+    p.mx_hi = ctx->mx_hi; p.mx_lo = ctx->mx_lo; p.mv_hi = ctx->mv_hi; p.mv_lo = ctx->mv_lo;
+    p.pos32 = ctx->pos32; p.vel32 = ctx->vel32;
+    for (int k = 0; k < 7; k++) p.pim[k] = ctx->pim[k];
+    for (int k = 0; k < 4; k++) p.pif[k] = ctx->pif[k];
+    np.n_act = n_act;
+    np.cap = cap;
+    np.act = act;
+    np.nnb = nnb;
+    np.list = list;
+    np.status = ctx->d_status;
+    nb::launch_predict_needed(np, st);
+    NB_CUDA(ctx, cudaGetLastError());
+    ctx->forms_valid = forms;
+    ctx->last_launches = 1;
+    return NB_OK;
+}
+
 int nb_set_frame(nb_ctx *ctx, const double *u)
 {
     if (!ctx || !u) return NB_ERR_ARG;
@@ -944,13 +1024,13 @@ int nb_get_tuned(nb_ctx *ctx, int index, nb_tuned *out)
 
 int nb_set_tuned(nb_ctx *ctx, const nb_tuned *t)
 {
-    if (!ctx || !t || t->mode < 0 || t->mode > 2 || t->flags < 0 || t->flags > 3 || t->act_class < 0 ||
+    if (!ctx || !t || t->mode < 0 || t->mode > 2 || t->flags < 0 || t->flags > 7 || t->act_class < 0 ||
         t->act_class > 62 || t->j_class < 0 || t->j_class > 62 || t->cfg.split < 0)
         return NB_ERR_ARG;
     const uint64_t key = tune_key(t->mode, t->flags, t->act_class, t->j_class);
     if (t->cfg.warps == 0) { ctx->tuned.erase(key); return NB_OK; }
     for (const auto &e : registry().all)
-        if (e.mode == t->mode && e.flags == t->flags && e.warps == t->cfg.warps && e.ipw == t->cfg.ipw &&
+        if (e.mode == t->mode && e.flags == (t->flags & 3) && e.warps == t->cfg.warps && e.ipw == t->cfg.ipw &&
             e.jtile == t->cfg.jtile && e.packed == t->cfg.packed) {
             ctx->tuned[key] = *t;
             return NB_OK;
@@ -1130,7 +1210,18 @@ int nb_plan_create(nb_ctx *ctx, int32_t n_clusters, const nb_cluster *cl, int mo
         act_sum += cl[c].n_act;
         j_max = std::max<int64_t>(j_max, cl[c].n_j);
     }
-    const nb_kcfg cfg = cfg_in ? *cfg_in : pick_cfg(ctx, mode, flags, std::max<int64_t>(act_sum, 1), j_max);
+    // tiling: the caller's, else the one nb_plan_autotune found for this
+    // batched size class, else that of a single call of the summed size
+    nb_kcfg cfg;
+    if (cfg_in) {
+        cfg = *cfg_in;
+    } else {
+        const auto it = ctx->cfg_set[mode]
+                            ? ctx->tuned.end()
+                            : ctx->tuned.find(tune_key(mode, flags | kBatchedClass,
+                                                       log2_floor(std::max<int64_t>(act_sum, 1)), log2_floor(j_max)));
+        cfg = it != ctx->tuned.end() ? it->second.cfg : pick_cfg(ctx, mode, flags, std::max<int64_t>(act_sum, 1), j_max);
+    }
     int idx = find_entry(mode, cfg, flags);
     if (idx < 0) return NB_ERR_UNSUPPORTED;
     bool odd = false;
@@ -1148,6 +1239,11 @@ int nb_plan_create(nb_ctx *ctx, int32_t n_clusters, const nb_cluster *cl, int mo
     p->mode = mode;
     p->entry = idx;
     p->e = &registry().all[idx];
+    p->clusters.assign(cl, cl + n_clusters);
+    p->cfg = nb_kcfg{p->e->warps, p->e->ipw, p->e->jtile, cfg.split, p->e->packed};
+    p->flags = flags;
+    p->act_sum = act_sum;
+    p->j_max = j_max;
     // Tile every cluster.  Splits are chosen for the whole batch: the number
     // of work items across clusters should cover the resident CTA slots.
     // The persistent kernel deals items to its CTAs round-robin (CTA k takes
@@ -1305,6 +1401,84 @@ int nb_regular_force_batched(nb_ctx *ctx, int32_t n_clusters, const nb_cluster *
     ctx->last_launches = rc == NB_OK ? nb_plan_launches(p) : 0;
     nb_plan_destroy(p);
     return rc != NB_OK ? rc : st;
+}
+
+int nb_plan_get_config(const nb_plan *p, nb_kcfg *out)
+{
+    if (!p || !out) return NB_ERR_ARG;
+    *out = p->cfg;
+    return NB_OK;
+}
+
+int nb_plan_autotune(nb_plan *p, int reps, nb_stream_t stream, nb_kcfg *best, float *best_ms)
+{
+    if (!p || reps <= 0) return NB_ERR_ARG;
+    nb_ctx *ctx = p->ctx;
+    if (!(ctx->forms_valid & mode_forms(p->mode))) { ctx->err = "form not predicted"; return NB_ERR_STATE; }
+    DeviceGuard guard(ctx->device);
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    bool odd = false;
+    for (const auto &c : p->clusters) odd |= (c.j_begin & 1) != 0;
+    const int nc = static_cast<int>(p->clusters.size());
+    cudaEvent_t a, b;
+    NB_CUDA(ctx, cudaEventCreate(&a));
+    NB_CUDA(ctx, cudaEventCreate(&b));
+    nb_kcfg win{0, 0, 0, 0, 0};
+    float win_ms = 0.f;
+    int rc = NB_OK;
+    Registry &r = registry();
+    for (size_t i = 0; i < r.all.size() && rc == NB_OK; i++) {
+        const KernelEntry &e = r.all[i];
+        if (e.mode != p->mode || e.flags != p->flags) continue;
+        if (e.packed >= 2 && odd) continue;   // j-pair layouts need even first slots
+        // j-split length in tiles: the plan's heuristic (0), powers of two up
+        // to the largest cluster's tile count, and that count (no split)
+        const int max_tiles = static_cast<int>((p->j_max + e.jtile - 1) / e.jtile);
+        std::vector<int> tpss{0};
+        for (int t = 1; t < max_tiles && t <= 64; t *= 2) tpss.push_back(t);
+        tpss.push_back(std::max(1, max_tiles));
+        for (int tps : tpss) {
+            const nb_kcfg cfg{e.warps, e.ipw, e.jtile, tps, e.packed};
+            nb_plan *q = nullptr;
+            const int cr = nb_plan_create(ctx, nc, p->clusters.data(), p->mode, &cfg, &q);
+            if (cr == NB_ERR_NOMEM) { cudaGetLastError(); continue; }   // this split's scratch does not fit
+            if (cr != NB_OK) { rc = cr; break; }
+            if (q->entry != static_cast<int>(i)) { nb_plan_destroy(q); continue; }
+            rc = nb_plan_run(q, stream);   // warm-up
+            if (rc == NB_OK) {
+                cudaEventRecord(a, st);
+                for (int k = 0; k < reps && rc == NB_OK; k++) rc = nb_plan_run(q, stream);
+                cudaEventRecord(b, st);
+                float t = 0.f;
+                cudaError_t ce = cudaEventSynchronize(b);
+                if (ce == cudaSuccess) ce = cudaEventElapsedTime(&t, a, b);
+                if (ce != cudaSuccess) rc = cuda_fail(ctx, ce, "timing events");
+                if (rc == NB_OK) {
+                    const int s = nb_sync_status(ctx, stream);
+                    if (s != NB_OK) rc = s;
+                }
+                t /= reps;
+                if (rc == NB_OK && (win.warps == 0 || t < win_ms)) { win = cfg; win_ms = t; }
+            }
+            nb_plan_destroy(q);
+        }
+    }
+    cudaEventDestroy(a);
+    cudaEventDestroy(b);
+    if (rc != NB_OK) return rc;
+    if (win.warps == 0) { ctx->err = "no compiled kernel for this plan"; return NB_ERR_UNSUPPORTED; }
+    // rebuild the plan with the winner (its captured graph, if any, is dropped)
+    nb_plan *q = nullptr;
+    rc = nb_plan_create(ctx, nc, p->clusters.data(), p->mode, &win, &q);
+    if (rc != NB_OK) return rc;
+    std::swap(*p, *q);
+    nb_plan_destroy(q);
+    nb_tuned t{p->mode, p->flags | kBatchedClass, log2_floor(std::max<int64_t>(p->act_sum, 1)),
+               log2_floor(p->j_max), win, win_ms};
+    ctx->tuned[tune_key(t.mode, t.flags, t.act_class, t.j_class)] = t;
+    if (best) *best = win;
+    if (best_ms) *best_ms = win_ms;
+    return NB_OK;
 }
 
 int nb_plan_launch(nb_plan *p, nb_stream_t stream)

@@ -15,6 +15,13 @@
 //    the mean start velocity of kFrameSamples particles spread evenly over the
 //    call's range (every block computes the same value, in the same order, so
 //    no launch or grid-wide step is added), or the context's stored frame.
+//  * predict_needed_kernel: the same prediction for only the slots that an
+//    irregular-force call reads (Sec. 3.5: the host library predicts only the
+//    particles it needs when they are few, the NPACT switch of Appendix C):
+//    one thread per (active particle, list slot).  A slot named by several
+//    threads is predicted by each of them with identical results: removing
+//    the duplicates costs more dependent global-memory round trips than the
+//    repeated FP64 work of the small calls this kernel is for.
 //  * merge_kernel: one warp per active particle of a cluster whose j-range
 //    was split over several work items; sums the per-split partial force,
 //    jerk and potential in a fixed order (float-float pairs for the float
@@ -97,6 +104,24 @@ __device__ void frame_velocity(const PredParams &p, double (&u)[3])
         for (int c = 0; c < 3; c++) p.frame[c] = u[c];
 }
 
+// Third-order Taylor polynomial of element j of the call's arrays (Horner
+// form of x0 + v0 dt + a dt^2/2 + ad dt^3/6 and v0 + a dt + ad dt^2/2), or
+// the given state itself for nb_set_predicted (a0 == nullptr).
+__device__ __forceinline__ void taylor(const PredParams &p, int64_t j, double (&x)[3], double (&v)[3])
+{
+    if (p.a0) {
+        const double dt = p.t - p.t0[j];
+        for (int k = 0; k < 3; k++) {
+            const double x0 = p.x0[3 * j + k], v0 = p.v0[3 * j + k];
+            const double a = p.a0[3 * j + k], ad = p.adot0[3 * j + k];
+            x[k] = fma(dt, fma(dt, fma(dt, ad * (1.0 / 6.0), a * 0.5), v0), x0);
+            v[k] = fma(dt, fma(dt, ad * 0.5, a), v0);
+        }
+    } else {
+        for (int k = 0; k < 3; k++) { x[k] = p.x0[3 * j + k]; v[k] = p.v0[3 * j + k]; }
+    }
+}
+
 __global__ void predict_kernel(const PredParams p)
 {
     double u[3];
@@ -107,19 +132,7 @@ __global__ void predict_kernel(const PredParams p)
     if (!__any_sync(0xffffffffu, live)) return;
     double x[3] = {0, 0, 0}, v[3] = {0, 0, 0};
     const double m = live ? p.m[j] : 0.0;
-    if (!live) {
-    } else if (p.a0) {
-        const double dt = p.t - p.t0[j];
-        for (int k = 0; k < 3; k++) {
-            const double x0 = p.x0[3 * j + k], v0 = p.v0[3 * j + k];
-            const double a = p.a0[3 * j + k], ad = p.adot0[3 * j + k];
-            // Horner form of x0 + v0 dt + a dt^2/2 + ad dt^3/6 and v0 + a dt + ad dt^2/2
-            x[k] = fma(dt, fma(dt, fma(dt, ad * (1.0 / 6.0), a * 0.5), v0), x0);
-            v[k] = fma(dt, fma(dt, ad * 0.5, a), v0);
-        }
-    } else {
-        for (int k = 0; k < 3; k++) { x[k] = p.x0[3 * j + k]; v[k] = p.v0[3 * j + k]; }
-    }
+    if (live) taylor(p, j, x, v);
     const int64_t s = p.offset + j;
     if ((p.forms & 1) && live) {
         p.pos64[s] = make_double4_32a(x[0], x[1], x[2], m);
@@ -165,6 +178,82 @@ __global__ void predict_kernel(const PredParams p)
         write_pairs<4>(p.pif, vals, s, live, even, partner_in);
     }
 }
+
+// Store slot s's values as its halves of float4 k of j-pair s / 2 in each of
+// the NQ pair-interleaved streams (stream q holds (v[2q], v[2q+1]) of both
+// slots of the pair), without touching the partner slot's halves.
+template <int NQ>
+__device__ __forceinline__ void write_pair_halves(float4 *const *streams, const float (&v)[2 * NQ], int64_t s)
+{
+    const int h = static_cast<int>(s & 1);
+#pragma unroll
+    for (int q = 0; q < NQ; q++) {
+        float *f = reinterpret_cast<float *>(streams[q] + (s >> 1));
+        f[h] = v[2 * q];
+        f[2 + h] = v[2 * q + 1];
+    }
+}
+
+__global__ void predict_needed_kernel(const NeededParams np)
+{
+    const PredParams &p = np.pp;
+    const int64_t per = static_cast<int64_t>(np.cap) + 1;   // the particle itself, then its list row
+    const int64_t t = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
+    if (t >= static_cast<int64_t>(np.n_act) * per) return;
+    const int64_t k = t / per;
+    const int e = static_cast<int>(t - k * per);
+    int64_t j;   // index in the range
+    if (e == 0) {
+        j = np.act[k];
+    } else {
+        const int nn = np.nnb[k];
+        if (nn < 0) {
+            if (e == 1) atomicOr(np.status, DEV_BAD_INPUT);
+            return;
+        }
+        if (e - 1 >= min(nn, np.cap)) return;
+        j = np.list[k * np.cap + (e - 1)];
+    }
+    if (j < 0 || j >= p.n) { atomicOr(np.status, DEV_BAD_INPUT); return; }
+    const int64_t s = p.offset + j;
+    double x[3], v[3], u[3];
+    taylor(p, j, x, v);
+    const double m = p.m[j];
+    for (int c = 0; c < 3; c++) u[c] = p.frame[c];
+    double vr[3];
+    for (int c = 0; c < 3; c++) vr[c] = v[c] - u[c];
+    if (p.forms & 1) {
+        p.pos64[s] = make_double4_32a(x[0], x[1], x[2], m);
+        p.vel64[s] = make_double4_32a(v[0], v[1], v[2], 0.0);
+    }
+    if (p.forms & 2) {
+        float xh[3], xl[3], vh[3], vl[3];
+        for (int c = 0; c < 3; c++) {
+            xh[c] = __double2float_rn(x[c]);
+            xl[c] = __double2float_rn(x[c] - static_cast<double>(xh[c]));
+            vh[c] = __double2float_rn(vr[c]);
+            vl[c] = __double2float_rn(vr[c] - static_cast<double>(vh[c]));
+        }
+        const float mh = __double2float_rn(m);
+        const float ml = __double2float_rn(m - static_cast<double>(mh));
+        p.mx_hi[s] = make_float4(xh[0], xh[1], xh[2], mh);
+        p.mx_lo[s] = make_float4(xl[0], xl[1], xl[2], ml);
+        p.mv_hi[s] = make_float4(vh[0], vh[1], vh[2], 0.f);
+        p.mv_lo[s] = make_float4(vl[0], vl[1], vl[2], 0.f);
+        const float vals[14] = {xh[0], xh[1], xh[2], mh, xl[0], xl[1], xl[2],
+                                vh[0], vh[1], vh[2], vl[0], vl[1], vl[2], 0.f};
+        write_pair_halves<7>(p.pim, vals, s);
+    }
+    if (p.forms & 4) {
+        const float vals[8] = {__double2float_rn(x[0]), __double2float_rn(x[1]), __double2float_rn(x[2]),
+                               __double2float_rn(m), __double2float_rn(vr[0]), __double2float_rn(vr[1]),
+                               __double2float_rn(vr[2]), 0.f};
+        p.pos32[s] = make_float4(vals[0], vals[1], vals[2], vals[3]);
+        p.vel32[s] = make_float4(vals[4], vals[5], vals[6], 0.f);
+        write_pair_halves<4>(p.pif, vals, s);
+    }
+}
+
 
 __global__ void merge_kernel(const MergeParams p)
 {
@@ -276,6 +365,17 @@ void launch_predict(const PredParams &p, cudaStream_t st)
     const int threads = 64;
     const int64_t blocks = (p.n + threads - 1) / threads;
     predict_kernel<<<static_cast<unsigned>(blocks), threads, 0, st>>>(p);
+}
+
+void launch_predict_needed(const NeededParams &p, cudaStream_t st)
+{
+    const int64_t threads_total = static_cast<int64_t>(p.n_act) * (static_cast<int64_t>(p.cap) + 1);
+    if (threads_total <= 0) return;
+    // 64-thread blocks, as for the full prediction: the FP64 polynomial is
+    // bound by the SMs it reaches
+    const int threads = 64;
+    const int64_t blocks = (threads_total + threads - 1) / threads;
+    predict_needed_kernel<<<static_cast<unsigned>(blocks), threads, 0, st>>>(p);
 }
 
 void launch_merge(const MergeParams &p, cudaStream_t st)

@@ -27,6 +27,17 @@ struct PredParams {
     float4 *pif[4];    // pair-interleaved FP32 streams
 };
 
+// Needed-only prediction: the slots an irregular-force call reads (the
+// active particles and the first min(nnb, cap) entries of their lists), in
+// the context's current frame (pp.keep_frame = 1).  A slot named several
+// times is predicted by each thread that names it, with the same result.
+struct NeededParams {
+    PredParams pp;                 // the range [pp.offset, pp.offset + pp.n) and its arrays
+    int32_t n_act, cap;
+    const int32_t *act, *nnb, *list;
+    int *status;                   // DEV_BAD_INPUT on an index outside the range or a negative count
+};
+
 struct MergeParams {
     ClusterDesc d0;                // single cluster (table == nullptr)
     const ClusterDesc *table;      // cluster table of a batched plan
@@ -39,6 +50,7 @@ struct MergeParams {
 };
 
 void launch_predict(const PredParams &p, cudaStream_t st);
+void launch_predict_needed(const NeededParams &p, cudaStream_t st);
 void launch_merge(const MergeParams &p, cudaStream_t st);
 
 // One compiled instantiation of the regular-force kernel.

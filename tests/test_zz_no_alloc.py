@@ -61,10 +61,10 @@ def test_noalloc_matches_regular_force_twice(workload, mode):
 
 
 def test_noalloc_takes_the_tuned_tiling(workload):
-    """With a tuned entry loaded for the call's size class (a 512-j tiling
-    split into 8 parts instead of the default), both calls run that tiling:
-    bit-identical results, and the default tiling's results differ in the
-    last bits (the summation order changed)."""
+    """With a tuned entry loaded for the call's size class (the exact pair
+    form, 512-j tiles, 8 tiles per j-split, instead of the default tiling),
+    both calls run that tiling: bit-identical results, which differ from the
+    default tiling's in the last bits (other velocity arithmetic)."""
     w = workload
     with Context(w.n) as ctx:
         d = upload(w)
@@ -73,7 +73,7 @@ def test_noalloc_takes_the_tuned_tiling(workload):
         t = B.nb_tuned()
         t.mode, t.flags = B.NB_MIXED, 0
         t.act_class, t.j_class = int(np.log2(w.n_act)), int(np.log2(w.n))
-        t.cfg = B.nb_kcfg(16, 2, 512, 4, 5)
+        t.cfg = B.nb_kcfg(16, 2, 512, 8, 2)
         B.nb_set_tuned(ctx.h, t)
         ref, ref_launches = _call(B.nb_regular_force, ctx, d, w, "mixed", w.cap)
         assert ref_launches == 2
