@@ -52,6 +52,9 @@ def parse_args():
     ap.add_argument("--no-forms", action="store_true", help="skip the FP64/FP32 side measurements")
     ap.add_argument("--cpu-sample", type=int, default=4096, help="active particles in the oracle sample")
     ap.add_argument("--no-e2e", action="store_true", help="skip the host-buffer measurement")
+    ap.add_argument("--no-side", action="store_true",
+                    help="skip the compact side workloads of the default line (batched clusters, offset cluster "
+                         "with hard pairs, block-step sweep)")
     ap.add_argument("--config", default="", help="kernel tiling warps,ipw,jtile,packed[,split] "
                                                  "(default: the autotuner's choice)")
     ap.add_argument("--no-tune", action="store_true", help="skip the autotuner (library default tiling)")
@@ -567,10 +570,56 @@ def run_ours(args):
         base, o, rows = cpu_baseline(w, args.cpu_sample)
         line["cpu_baseline"] = base
         line["accuracy_vs_oracle"] = {m: accuracy(g, o, rows, w.cap) for m, g in outs.items()}
+    if not args.no_side and world == 1:
+        line.update(side_workloads(args, peak))
     if world > 1:
         torch.distributed.barrier()
         torch.distributed.destroy_process_group()
     print(json.dumps(line), flush=True)
+
+
+def side_workloads(args, peak):
+    """Compact results of the other benchmark configurations, each bounded to
+    a few seconds: the 64-cluster batched launch (cfg4), the offset cluster
+    with hard pairs at 4096 active in every form (cfg5) and the block-step
+    sweep of active-set sizes (cfg2).  Each is timed outside the headline's
+    timed region; the full records come from --workload batched64 /
+    offset-pairs / blockstep."""
+    out = {}
+    t0 = time.perf_counter()
+    b = batched_result(args, steps=5)
+    acc = b["accuracy_vs_oracle"]
+    out["cfg4"] = {
+        "workload": "64 Plummer clusters, N 1024..32768, n_act 8..N, seed 4 (N_total %d, n_act_total %d)"
+                    % (b["config"]["N_total"], b["config"]["n_act_total"]),
+        "graph_ms": b["ms_per_step"], "value": b["value"],
+        "frac_fp32_peak": FLOPS_PER_INTERACTION * b["value"] / 1e12 / peak,
+        "per_cluster_ms": b["per_cluster_launches"]["ms_per_step"], "speedup_vs_per_cluster": b["speedup_vs_per_cluster"],
+        "plan_tiling": b["plan_tiling"], "F_max": acc["F_max"], "J_max": acc["J_max"],
+        "list_mismatches": acc["list_mismatches"], "rows_beyond_relative_bar": acc["rows_beyond_relative_bar"],
+        "rows_beyond_u_times_term_length_sum": acc["rows_beyond_u_times_term_length_sum"],
+        "graph_vs_per_cluster_list_mismatches": b["graph_vs_per_cluster_list_mismatches"],
+        "seconds": time.perf_counter() - t0}
+    t0 = time.perf_counter()
+    o = offset_result(args, n_acts=(4096,), steps=3)
+    out["cfg5"] = {"workload": "Plummer N=262144 at |x_c|=1e3, 10% hard pairs, 4096 active, oracle on all 4096 rows",
+                   "forms": {k.split("@")[0]: {"value": f["value"], "kernel_ms": f["kernel_ms"],
+                                                "frac_fp32_peak": FLOPS_PER_INTERACTION * f["value"] / 1e12 / peak,
+                                                "F_max": f["accuracy"]["F_max"], "J_max": f["accuracy"]["J_max"],
+                                                "list_mismatches": f["accuracy"]["list_mismatches"]}
+                             for k, f in o["forms"].items()},
+                   "seconds": time.perf_counter() - t0}
+    t0 = time.perf_counter()
+    bs = blockstep_result(args, steps=3)
+    out["cfg2"] = {"workload": "Plummer N=16384, random active subsets, prediction + force per step",
+                   "sizes": [{"n_act": r["n_act"], "mixed_graph_step_us": r["mixed"]["graph_step_us"],
+                              "mixed_step_us_l2_flushed": r["mixed"]["step_ms"] * 1e3,
+                              "fp64_graph_step_us": r["fp64"]["graph_step_us"],
+                              "mixed_F_max": r["mixed"]["accuracy"]["F_max"],
+                              "mixed_J_max": r["mixed"]["accuracy"]["J_max"],
+                              "list_mismatches": r["mixed"]["accuracy"]["list_mismatches"]} for r in bs["sizes"]],
+                   "seconds": time.perf_counter() - t0}
+    return out
 
 
 def run_reference(args):
@@ -623,6 +672,10 @@ def _timed_events(fn, steps, flush, stream, torch):
 
 
 def run_batched(args):
+    print(json.dumps(batched_result(args)), flush=True)
+
+
+def batched_result(args, steps=None):
     """64 independent clusters (N log-uniform in [1024, 32768], n_act log-uniform
     in [8, N]): prediction of all clusters in one launch plus the regular force
     of all of them as one persistent launch (and the split merge) replayed from
@@ -686,7 +739,7 @@ def run_batched(args):
                 for _ in range(max(args.warmup, 3)):
                     predict(); B.nb_plan_launch(plan, stream=stream, ctx=ctx.h)
                 graph_ms = _timed_events(lambda: (predict(), B.nb_plan_launch(plan, stream=stream, ctx=ctx.h)),
-                                         args.steps, flush, stream, torch)
+                                         steps or args.steps, flush, stream, torch)
                 plan_launches = 1 + B.nb_plan_launches(plan)
                 stream.synchronize()
                 graph_out = [{k: v.cpu().numpy() for k, v in out.items() if v is not None} for _, _, out in keep]
@@ -700,7 +753,7 @@ def run_batched(args):
                                        None, out["nnb"], out["list"], out["ovf"], stream)
             for _ in range(max(args.warmup, 3)):
                 per_cluster()
-            loop_ms = _timed_events(per_cluster, args.steps, flush, stream, torch)
+            loop_ms = _timed_events(per_cluster, steps or args.steps, flush, stream, torch)
             stream.synchronize()
             loop_out = [{k: v.cpu().numpy() for k, v in out.items() if v is not None} for _, _, out in keep]
         st = ctx.sync_status(stream)
@@ -710,17 +763,24 @@ def run_batched(args):
     # oracle (FP64, all host cores)
     import oracle
     mism = sum(int(np.any(a[k] != b[k])) for a, b in zip(graph_out, loop_out) for k in ("nnb", "list", "ovf"))
-    eFs, eJs, bad = [], [], 0
+    eFs, eJs, bad, beyond, outside = [], [], 0, 0, 0
+    u = 2.0 ** -24
     t0 = time.perf_counter()
     for w, go in zip(ws, graph_out):
         x, v = oracle.predict(w.x0, w.v0, w.a0, w.adot0, w.t0, w.t)
         o = oracle.regular(x, v, w.m, w.act, w.h, cap=w.cap)
+        SF, SJ = oracle.regular_mag(x, v, w.m, w.act, w.h)
         acc = accuracy(go, o, np.arange(w.n_act), w.cap)
         eFs.append(acc["F_max"]); eJs.append(acc["J_max"]); bad += acc["list_mismatches"]
+        dF = np.linalg.norm(go["F"] - o["F"], axis=1); nF = np.linalg.norm(o["F"], axis=1)
+        dJ = np.linalg.norm(go["J"] - o["J"], axis=1); nJ = np.linalg.norm(o["J"], axis=1)
+        rel_ok = (dF <= 1e-6 * nF) & (dJ <= 1e-5 * nJ)
+        beyond += int((~rel_ok).sum())
+        outside += int((~(rel_ok | ((dF <= u * SF) & (dJ <= u * SJ)))).sum())
     oracle_s = time.perf_counter() - t0
-    print(json.dumps({
+    return {
         "metric": "regular-force interactions/s, 64 independent clusters, one persistent launch in a CUDA graph",
-        "value": inter / (g / 1e3), "unit": "interactions/s", "n_gpus": 1, "steps": args.steps,
+        "value": inter / (g / 1e3), "unit": "interactions/s", "n_gpus": 1, "steps": steps or args.steps,
         "warmup": max(args.warmup, 3), "ms_per_step": g, "higher_is_better": True, "dtype": "f32",
         "data": "synthetic", "status": st,
         "config": {"workload": "64 equal-mass Plummer clusters, N log-uniform in [1024, 32768], n_act "
@@ -733,12 +793,17 @@ def run_batched(args):
         "graph_launches_per_step": plan_launches, "speedup_vs_per_cluster": l / g,
         "plan_tiling": plan_cfg, "autotune": tuned,
         "accuracy_vs_oracle": {"rows": "every row of every cluster", "F_max": max(eFs), "J_max": max(eJs),
-                               "list_mismatches": bad, "oracle_seconds": oracle_s},
+                               "list_mismatches": bad, "rows_beyond_relative_bar": beyond,
+                               "rows_beyond_u_times_term_length_sum": outside, "oracle_seconds": oracle_s},
         "graph_vs_per_cluster_list_mismatches": mism,
-    }), flush=True)
+    }
 
 
 def run_offset_pairs(args):
+    print(json.dumps(offset_result(args)), flush=True)
+
+
+def offset_result(args, n_acts=None, steps=None):
     """N = 262144 cluster offset to |x_c| = 1e3 with 10% of the particles in hard
     pairs: FP32, two-float (default and exact pair form) and FP64 forms, their
     throughput and their errors against the oracle on sampled rows."""
@@ -753,7 +818,7 @@ def run_offset_pairs(args):
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
     x, v = oracle.predict(full.x0, full.v0, full.a0, full.adot0, full.t0, full.t)
     res = {}
-    for n_act in (4096, full.n):
+    for n_act in (n_acts or (4096, full.n)):
         w = full if n_act == full.n else inputs.subset(full, n_act, 5)
         rows = np.arange(w.n_act) if w.n_act <= 4096 else \
             np.sort(np.random.default_rng(5).choice(w.n_act, 4096, replace=False))
@@ -764,20 +829,20 @@ def run_offset_pairs(args):
             if not cfg and mode != "fp64" and not args.no_tune:
                 r.autotune()
             r.predict(); r.force()
-            k = 1 if mode == "fp64" and n_act == full.n else max(2, min(args.steps, 5))
+            k = 1 if mode == "fp64" and n_act == full.n else (steps or max(2, min(args.steps, 5)))
             ms = statistics.mean(r.timed(k, flush)[1])
             g = r.outputs()
             r.close()
             res[f"{label}@{n_act}"] = {"value": w.n * w.n_act / (ms / 1e3), "kernel_ms": ms, "tiling": r.cfg,
                                        "accuracy": accuracy(g, o, rows, w.cap)}
-    print(json.dumps({
+    return {
         "metric": "regular-force interactions/s and errors vs the FP64 oracle, offset cluster with hard pairs",
         "unit": "interactions/s", "n_gpus": 1, "dtype": "f32/f64", "data": "synthetic",
         "config": {"workload": "equal-mass Plummer, N=262144, centre at |x|=1e3, 10% in hard pairs "
                                "(separations 1e-5..1e-2), ~128 neighbours, cap 256, seed 5",
-                   "n_act": [4096, full.n], "oracle_rows": "all 4096 / a seeded 4096-row sample"},
+                   "n_act": list(n_acts or (4096, full.n)), "oracle_rows": "all 4096 / a seeded 4096-row sample"},
         "forms": res,
-    }), flush=True)
+    }
 
 
 def run_velocity(args):
@@ -878,6 +943,10 @@ def run_irregular(args):
 
 
 def run_blockstep(args):
+    print(json.dumps(blockstep_result(args)), flush=True)
+
+
+def blockstep_result(args, steps=None):
     """Block-step active subsets of the N = 16384 Plummer cluster (n_act = 16 ..
     16384, steps 2^-3 .. 2^-12): prediction plus regular force per step for the
     two-float form (autotuned per size class) and the FP64 form, with errors
@@ -903,7 +972,7 @@ def run_blockstep(args):
                 r.autotune()
             for _ in range(3):
                 r.predict(); r.force()
-            step_ms, force_ms = r.timed(max(3, min(args.steps, 10)), flush)
+            step_ms, force_ms = r.timed(steps or max(3, min(args.steps, 10)), flush)
             g = r.outputs()
             graph_us = r.graph_step_us()
             r.close()
@@ -912,14 +981,14 @@ def run_blockstep(args):
                          "interactions_per_s": w.n * n_act / (statistics.mean(step_ms) / 1e3), "tiling": r.cfg,
                          "accuracy": accuracy(g, o, np.arange(n_act), w.cap)}
         res.append(row)
-    print(json.dumps({
+    return {
         "metric": "regular-force interactions/s per block step (prediction included) across active-set sizes",
         "unit": "interactions/s", "n_gpus": 1, "dtype": "f32/f64", "data": "synthetic",
         "config": {"workload": "equal-mass Plummer N=16384, seed 2, ~64 neighbours, cap 256, random active subsets",
                    "l2": "flushed between timed steps; graph_step_us: 20 steps replayed from one CUDA graph, "
                          "L2 warm"},
         "sizes": res,
-    }), flush=True)
+    }
 
 
 def _graph_us(fn, device, reps=20):

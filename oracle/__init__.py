@@ -105,7 +105,8 @@ def _declare(lib):
     lib.orc_regular.argtypes = [i64, P, P, P, i32, P, P, P, i32, P, P, P, P, P, P, cint]
     lib.orc_irregular.argtypes = [i64, P, P, P, i32, P, P, P, P, P, cint]
     lib.orc_full.argtypes = [i64, P, P, P, i32, P, P, P, P, cint]
-    for f in (lib.orc_predict, lib.orc_regular, lib.orc_irregular, lib.orc_full):
+    lib.orc_regular_mag.argtypes = [i64, P, P, P, i32, P, P, P, P, P, cint]
+    for f in (lib.orc_predict, lib.orc_regular, lib.orc_irregular, lib.orc_full, lib.orc_regular_mag):
         f.restype = cint
     lib.orc_default_threads.argtypes = []
     lib.orc_default_threads.restype = cint
@@ -184,6 +185,22 @@ def irregular(x, v, m, act, h, dtr=None, threads=0):
     _check(lib.orc_irregular(n, _ptr(x), _ptr(v), _ptr(m), na, _ptr(act), _ptr(h), _ptr(dtr),
                              _ptr(F), _ptr(J), int(threads)), "irregular")
     return F, J
+
+
+def regular_mag(x, v, m, act, h, dtr=None, threads=0):
+    """Sums of the lengths of the regular force and jerk terms of each active
+    particle (SF, SJ): the condition numbers of the regular sums are SF/|F|
+    and SJ/|J|."""
+    lib = _load()
+    x = _f64(x); n = x.shape[0]
+    v, m = _f64(v, (n, 3)), _f64(m, (n,))
+    act = np.ascontiguousarray(act, dtype=np.int32); na = act.shape[0]
+    h = _f64(h, (na,))
+    dtr = None if dtr is None else _f64(dtr, (na,))
+    SF = np.zeros(na); SJ = np.zeros(na)
+    _check(lib.orc_regular_mag(n, _ptr(x), _ptr(v), _ptr(m), na, _ptr(act), _ptr(h), _ptr(dtr),
+                               _ptr(SF), _ptr(SJ), int(threads)), "regular_mag")
+    return SF, SJ
 
 
 def full(x, v, m, act, with_pot=False, threads=0):

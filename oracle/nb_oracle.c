@@ -267,6 +267,63 @@ int orc_full(int64_t n, const double *x, const double *v, const double *m,
     return status;
 }
 
+/*
+ * Conditioning of the regular sums: for each active particle, the sums over
+ * its regular set (the j that orc_regular sums) of the lengths of the
+ * individual force and jerk terms,
+ *   SF_i = sum_j |m_j R / |R|^3|,
+ *   SJ_i = sum_j |m_j [ V / |R|^3 - 3 (R.V) R / |R|^5 ]|.
+ * SF_i / |F_i| and SJ_i / |J_i| are the condition numbers of the two sums: a
+ * sum whose terms each carry a relative rounding error e has an absolute
+ * error of at most e SF_i (e SJ_i), however much the terms cancel.  Used to
+ * state the tolerance of working-precision pair terms on rows whose regular
+ * force or jerk nearly cancels.
+ */
+int orc_regular_mag(int64_t n, const double *x, const double *v, const double *m,
+                    int32_t n_act, const int32_t *act, const double *h,
+                    const double *dtr, double *SF, double *SJ, int nthreads)
+{
+    if (n < 0 || n_act < 0) return ORC_ERR_ARG;
+    if (n_act > 0 && (!x || !v || !m || !act || !h || !SF || !SJ)) return ORC_ERR_ARG;
+    for (int32_t a = 0; a < n_act; a++)
+        if (act[a] < 0 || act[a] >= n) return ORC_ERR_ARG;
+    int status = ORC_OK;
+#ifdef _OPENMP
+    int nt = nthreads > 0 ? nthreads : omp_get_num_procs();
+#pragma omp parallel for schedule(dynamic, 8) num_threads(nt)
+#endif
+    for (int32_t a = 0; a < n_act; a++) {
+        int64_t i = act[a];
+        double sf = 0.0, sj = 0.0;
+        const double *dtr_i = dtr ? &dtr[a] : NULL;
+        for (int64_t j = 0; j < n; j++) {
+            if (j == i) continue;
+            double R[3], V[3];
+            for (int k = 0; k < 3; k++) {
+                R[k] = x[3 * j + k] - x[3 * i + k];
+                V[k] = v[3 * j + k] - v[3 * i + k];
+            }
+            if (is_neighbour(R, V, h[a], dtr_i)) continue;
+            double r2 = dot3(R, R);
+            if (r2 == 0.0) {
+#ifdef _OPENMP
+#pragma omp atomic write
+#endif
+                status = ORC_ERR_COINCIDENT;
+                continue;
+            }
+            double r = sqrt(r2);
+            double fJ[3];
+            for (int k = 0; k < 3; k++) fJ[k] = m[j] * (V[k] / (r2 * r) - 3.0 * dot3(R, V) * R[k] / (r2 * r2 * r));
+            sf += m[j] / r2;   /* |m R / |R|^3| */
+            sj += sqrt(dot3(fJ, fJ));
+        }
+        SF[a] = sf;
+        SJ[a] = sj;
+    }
+    return status;
+}
+
 /* Number of OpenMP threads a call with nthreads <= 0 uses (1 without OpenMP). */
 int orc_default_threads(void)
 {

@@ -9,11 +9,14 @@
 // access, not by arithmetic.
 //
 // Forms: FP64 throughout; two-float coordinates and mass (Sec. 3.5 keeps
-// two-float coordinates for this sum, since close pairs live here) differenced
-// exactly in FP64, with FP64 terms (the few neighbours' forces cancel, so an
-// FP32 mass alone cost ~6e-7 with Kroupa masses): a pair at 1e-5 separation 1e3 from the origin keeps the ~48 bits of
-// the two-float coordinates, where FP32 terms lost a further ~1e-6; plain FP32
-// differences and terms.
+// two-float coordinates for this sum, since close pairs live here) with the
+// pair terms in float-float arithmetic (unevaluated sums of two FP32 values,
+// about 46 significant bits) on the FP32 pipe: the irregular sum of a few
+// neighbours cancels (an FP32 mass alone cost ~6e-7 with Kroupa masses, FP32
+// terms ~1e-6 at 1e-5 separations 1e3 from the origin), and on GB300 a
+// float-float term of ~350 FP32 operations costs a fraction of the ~40 FP64
+// operations of an FP64 term (the FP64 pipe runs at 1/64 of the FP32 rate);
+// plain FP32 differences and terms.
 #include <cfloat>
 
 #include "nb_irr.cuh"
@@ -54,6 +57,151 @@ __device__ __forceinline__ void add_term_f(IrrTerm &a, float m, const float dx[3
     a.p += static_cast<double>(mr);
 }
 
+// ------------------------------------------------------------- float-float
+// A value h + l held as two FP32 numbers with |l| <= ulp(h)/2 after
+// normalisation.  The error-free transformations are the published ones:
+// Knuth's TwoSum, Dekker's FastTwoSum and the FMA form of the exact product
+// (the product's rounding error is fma(a, b, -p)).
+struct FF {
+    float h, l;
+};
+
+__device__ __forceinline__ FF two_sum(float a, float b)
+{
+    const float s = __fadd_rn(a, b);
+    const float bp = __fsub_rn(s, a);
+    return {s, __fadd_rn(__fsub_rn(a, __fsub_rn(s, bp)), __fsub_rn(b, bp))};
+}
+__device__ __forceinline__ FF fast_two_sum(float a, float b)   // |a| >= |b| (or a = 0)
+{
+    const float s = __fadd_rn(a, b);
+    return {s, __fsub_rn(b, __fsub_rn(s, a))};
+}
+__device__ __forceinline__ FF two_prod(float a, float b)
+{
+    const float p = __fmul_rn(a, b);
+    return {p, __fmaf_rn(a, b, -p)};
+}
+__device__ __forceinline__ FF ffadd(FF a, FF b)
+{
+    FF s = two_sum(a.h, b.h);
+    return fast_two_sum(s.h, __fadd_rn(s.l, __fadd_rn(a.l, b.l)));
+}
+__device__ __forceinline__ FF ffmul(FF a, FF b)
+{
+    FF p = two_prod(a.h, b.h);
+    return fast_two_sum(p.h, __fmaf_rn(a.h, b.l, __fmaf_rn(a.l, b.h, p.l)));
+}
+__device__ __forceinline__ FF ffmul_f(FF a, float b)
+{
+    FF p = two_prod(a.h, b);
+    return fast_two_sum(p.h, __fmaf_rn(a.l, b, p.l));
+}
+// (ah + al) - (bh + bl) of two two-float numbers, normalised.
+__device__ __forceinline__ FF ffdiff2(float ah, float al, float bh, float bl)
+{
+    FF s = two_sum(ah, -bh);
+    return fast_two_sum(s.h, __fadd_rn(s.l, __fsub_rn(al, bl)));
+}
+// 1/sqrt(x): the FP32 reciprocal square root y refined by one Newton step
+// evaluated in float-float, y + y (1 - x y^2) / 2 (1 - q.h is exact for
+// q = x y^2 near 1, so the correction carries the residual's full precision).
+__device__ __forceinline__ FF ffrsqrt(FF x)
+{
+    const float y = rsqrtf(x.h);
+    const FF q = ffmul(x, two_prod(y, y));
+    const float d = __fsub_rn(__fsub_rn(1.0f, q.h), q.l);
+    return fast_two_sum(y, __fmul_rn(__fmul_rn(y, d), 0.5f));
+}
+
+// Irregular sum of the two-float form, float-float pair terms and sums.
+template <bool POT>
+__global__ void __launch_bounds__(256) irr_ff_kernel(const IrrParams p)
+{
+    const int lane = threadIdx.x & 31;
+    const int64_t warps = static_cast<int64_t>(gridDim.x) * (blockDim.x >> 5);
+    const float4 *xh = reinterpret_cast<const float4 *>(p.js.s[0]);
+    const float4 *xl = reinterpret_cast<const float4 *>(p.js.s[1]);
+    const float4 *vh = reinterpret_cast<const float4 *>(p.js.s[2]);
+    const float4 *vl = reinterpret_cast<const float4 *>(p.js.s[3]);
+    for (int64_t i = static_cast<int64_t>(blockIdx.x) * (blockDim.x >> 5) + (threadIdx.x >> 5); i < p.n_act;
+         i += warps) {
+        const int a = p.act[i];
+        const int nn = p.nnb[i];
+        if (a < 0 || a >= p.n_j || nn < 0) {
+            if (lane == 0) atomicOr(p.status, DEV_BAD_INPUT);
+            continue;
+        }
+        const int k = min(nn, p.cap);
+        const int64_t si = p.j_begin + a;
+        const int32_t *row = p.list + i * static_cast<int64_t>(p.cap);
+        const float4 ih = xh[si], il = xl[si], jh = vh[si], jl = vl[si];
+        FF acc[8];
+        for (int c = 0; c < 8; c++) acc[c] = FF{0.f, 0.f};
+        for (int e = lane; e < k; e += 32) {
+            const int j = row[e];
+            if (j < 0 || j >= p.n_j || j == a) { atomicOr(p.status, DEV_BAD_INPUT); continue; }
+            const int64_t sj = p.j_begin + j;
+            const float4 ah = xh[sj], al = xl[sj], bh = vh[sj], bl = vl[sj];
+            const FF dx[3] = {ffdiff2(ah.x, al.x, ih.x, il.x), ffdiff2(ah.y, al.y, ih.y, il.y),
+                              ffdiff2(ah.z, al.z, ih.z, il.z)};
+            const FF dv[3] = {ffdiff2(bh.x, bl.x, jh.x, jl.x), ffdiff2(bh.y, bl.y, jh.y, jl.y),
+                              ffdiff2(bh.z, bl.z, jh.z, jl.z)};
+            const FF r2 = ffadd(ffadd(ffmul(dx[0], dx[0]), ffmul(dx[1], dx[1])), ffmul(dx[2], dx[2]));
+            const FF rinv = ffrsqrt(r2);
+            const FF rinv2 = ffmul(rinv, rinv);
+            const FF mr = ffmul(FF{ah.w, al.w}, rinv);   // two-float mass
+            const FF mr3 = ffmul(mr, rinv2);
+            const FF rv = ffadd(ffadd(ffmul(dx[0], dv[0]), ffmul(dx[1], dv[1])), ffmul(dx[2], dv[2]));
+            const FF alpha = ffmul_f(ffmul(rv, rinv2), -3.0f);
+#pragma unroll
+            for (int c = 0; c < 3; c++) {
+                acc[c] = ffadd(acc[c], ffmul(mr3, dx[c]));
+                acc[3 + c] = ffadd(acc[3 + c], ffmul(mr3, ffadd(dv[c], ffmul(alpha, dx[c]))));
+            }
+            if (POT) acc[6] = ffadd(acc[6], mr);
+        }
+        // Reduce-scatter of the eight float-float slots over the lanes (as in
+        // the FP64 form): lane L ends with slot 4 b4 + 2 b3 + b2 of its lane
+        // bits summed over all lanes, in 9 float-float additions per lane.
+        FF k4[4], k2[2];
+        {
+            const bool lo = (lane & 16) == 0;
+#pragma unroll
+            for (int c = 0; c < 4; c++) {
+                const FF send = lo ? acc[c + 4] : acc[c];
+                const FF got{__shfl_xor_sync(0xffffffffu, send.h, 16), __shfl_xor_sync(0xffffffffu, send.l, 16)};
+                k4[c] = ffadd(lo ? acc[c] : acc[c + 4], got);
+            }
+        }
+        {
+            const bool lo = (lane & 8) == 0;
+#pragma unroll
+            for (int c = 0; c < 2; c++) {
+                const FF send = lo ? k4[c + 2] : k4[c];
+                const FF got{__shfl_xor_sync(0xffffffffu, send.h, 8), __shfl_xor_sync(0xffffffffu, send.l, 8)};
+                k2[c] = ffadd(lo ? k4[c] : k4[c + 2], got);
+            }
+        }
+        FF k1;
+        {
+            const bool lo = (lane & 4) == 0;
+            const FF send = lo ? k2[1] : k2[0];
+            const FF got{__shfl_xor_sync(0xffffffffu, send.h, 4), __shfl_xor_sync(0xffffffffu, send.l, 4)};
+            k1 = ffadd(lo ? k2[0] : k2[1], got);
+        }
+        for (int o = 2; o > 0; o >>= 1)
+            k1 = ffadd(k1, FF{__shfl_xor_sync(0xffffffffu, k1.h, o), __shfl_xor_sync(0xffffffffu, k1.l, o)});
+        const int comp = 4 * ((lane >> 4) & 1) + 2 * ((lane >> 3) & 1) + ((lane >> 2) & 1);
+        if ((lane & 3) == 0) {
+            const double val = static_cast<double>(k1.h) + static_cast<double>(k1.l);
+            if (comp < 3) p.F[3 * i + comp] = val;
+            else if (comp < 6) p.J[3 * i + comp - 3] = val;
+            else if (POT && comp == 6) p.pot[i] = val;
+        }
+    }
+}
+
 template <int MODE, bool POT>
 __global__ void __launch_bounds__(256) irr_kernel(const IrrParams p)
 {
@@ -83,27 +231,6 @@ __global__ void __launch_bounds__(256) irr_kernel(const IrrParams p)
                 const double dv[3] = {vj.x - vi.x, vj.y - vi.y, vj.z - vi.z};
                 const double r2 = dx[0] * dx[0] + dx[1] * dx[1] + dx[2] * dx[2];
                 add_term(t, xj.w, rsqrt(r2), dx, dv);
-            }
-        } else if (MODE == 1) {   // two-float coordinates, exact FP64 differences, FP64 terms
-            const float4 *xh = reinterpret_cast<const float4 *>(p.js.s[0]);
-            const float4 *xl = reinterpret_cast<const float4 *>(p.js.s[1]);
-            const float4 *vh = reinterpret_cast<const float4 *>(p.js.s[2]);
-            const float4 *vl = reinterpret_cast<const float4 *>(p.js.s[3]);
-            const float4 ih = xh[si], il = xl[si], jh = vh[si], jl = vl[si];
-            for (int e = lane; e < k; e += 32) {
-                const int j = row[e];
-                if (j < 0 || j >= p.n_j || j == a) { atomicOr(p.status, DEV_BAD_INPUT); continue; }
-                const int64_t sj = p.j_begin + j;
-                const float4 ah = xh[sj], al = xl[sj], bh = vh[sj], bl = vl[sj];
-                // differences of FP32 values are exact in FP64, so these are the
-                // two-float differences without further rounding
-                auto d2 = [](float a, float b, float c, float e) {
-                    return (static_cast<double>(a) - b) + (static_cast<double>(c) - e);
-                };
-                const double dx[3] = {d2(ah.x, ih.x, al.x, il.x), d2(ah.y, ih.y, al.y, il.y), d2(ah.z, ih.z, al.z, il.z)};
-                const double dv[3] = {d2(bh.x, jh.x, bl.x, jl.x), d2(bh.y, jh.y, bl.y, jl.y), d2(bh.z, jh.z, bl.z, jl.z)};
-                const double r2 = dx[0] * dx[0] + dx[1] * dx[1] + dx[2] * dx[2];
-                add_term(t, static_cast<double>(ah.w) + al.w, rsqrt(r2), dx, dv);   // two-float mass
             }
         } else {   // FP32
             const float4 *x = reinterpret_cast<const float4 *>(p.js.s[0]);
@@ -167,7 +294,11 @@ cudaError_t launch_irregular(const IrrParams &p, int mode, int sm_count, cudaStr
     const int64_t want = (static_cast<int64_t>(p.n_act) + 7) / 8;   // 8 warps (active particles) per block
     const int grid = static_cast<int>(std::min<int64_t>(want, static_cast<int64_t>(sm_count) * 8));
     if (mode == 0) return launch_mode<0>(p, grid, st);
-    if (mode == 1) return launch_mode<1>(p, grid, st);
+    if (mode == 1) {
+        if (p.pot) irr_ff_kernel<true><<<grid, 256, 0, st>>>(p);
+        else irr_ff_kernel<false><<<grid, 256, 0, st>>>(p);
+        return cudaGetLastError();
+    }
     return launch_mode<2>(p, grid, st);
 }
 

@@ -102,6 +102,41 @@ def compare(g, o, cap, mode, rows=None, pot=False, lists=True):
     return eF, eJ
 
 
+# Unit roundoff of FP32.  A float-form pair term carries a relative rounding
+# error of up to ~10 u (the approximate reciprocal square root enters r^-3
+# three times; the differences, r^2 and the products add a few u), so on a
+# row whose regular sum cancels to a small fraction of the sum of its term
+# lengths S (condition number S / |F|), no FP32 term arithmetic reaches the
+# per-particle relative bar; such a row is held to an absolute error of
+# u * S instead (the per-term errors, largely independent, sum to well under
+# their worst case over the hundreds of dominant terms).
+U32 = 2.0 ** -24
+
+
+def compare_conditioned(g, o, SF, SJ, cap, mode):
+    """compare() for rows that may be ill-conditioned: lists exact; each row
+    within the relative bar of `mode`, or within u * S (S = SF, SJ from
+    oracle.regular_mag).  Returns the rows that needed the second bound,
+    with their errors and condition numbers."""
+    assert np.array_equal(g["nnb"], o["nnb"]), "neighbour counts differ"
+    assert np.array_equal(g["ovf"], o["ovf"]), "overflow flags differ"
+    k = np.minimum(o["nnb"], cap)
+    filled = np.arange(cap)[None, :] < k[:, None]
+    assert np.array_equal(np.where(filled, g["list"], -1), np.where(filled, o["list"], -1)), "lists differ"
+    ftol, jtol = TOL[mode]
+    dF = np.linalg.norm(g["F"] - o["F"], axis=1)
+    dJ = np.linalg.norm(g["J"] - o["J"], axis=1)
+    nF = np.linalg.norm(o["F"], axis=1)
+    nJ = np.linalg.norm(o["J"], axis=1)
+    okF = (dF <= ftol * nF) | (dF <= U32 * SF)
+    okJ = (dJ <= jtol * nJ) | (dJ <= U32 * SJ)
+    bad = np.nonzero(~(okF & okJ))[0]
+    assert bad.size == 0, [(int(r), dF[r] / nF[r], dF[r] / SF[r], dJ[r] / nJ[r], dJ[r] / SJ[r]) for r in bad[:5]]
+    cond = np.nonzero((dF > ftol * nF) | (dJ > jtol * nJ))[0]
+    return [(int(r), float(dF[r] / nF[r]), float(SF[r] / nF[r]), float(dJ[r] / nJ[r]), float(SJ[r] / nJ[r]))
+            for r in cond]
+
+
 def list_mismatches(g, o, cap, rows=None):
     """Number of active particles whose count or stored list differs."""
     sel = (lambda a: a) if rows is None else (lambda a: a[rows])

@@ -85,6 +85,28 @@ def test_two_float_irregular_force_on_hard_pairs_far_from_the_origin():
     assert rel_err(irr["J"], oJ).max() <= jtol
 
 
+@pytest.mark.parametrize("case", ["config2", "hard_pairs_offset"])
+def test_two_float_irregular_force_has_float_float_accuracy(case):
+    """The two-float form sums float-float pair terms (about 46 significant
+    bits from two FP32 values): every row within 1e-9 of the oracle's
+    irregular sum, three orders below the two-float tolerances.  The bar: each
+    float-float operation rounds at ~2^-46, a term is ~20 operations deep
+    (~1e-12), and the irregular sums here cancel to no less than ~1e-3 of the
+    sum of their terms' lengths."""
+    if case == "config2":
+        w = inputs.config2(n_act=1024)
+    else:
+        w = inputs.cluster(20000, 47, 64, 256, offset=1e3, pair_frac=0.1,
+                           act=np.arange(0, 20000, 7, dtype=np.int32))
+    reg, irr, st = _run(w, "mixed", pot=True)
+    assert st == 0 and not reg["ovf"].any()
+    x, v = oracle_predicted(w)
+    oF, oJ = oracle.irregular(x, v, w.m, w.act, w.h)
+    eF, eJ = rel_err(irr["F"], oF), rel_err(irr["J"], oJ)
+    print(case, "float-float irregular max rel err F %.2e J %.2e" % (eF.max(), eJ.max()))
+    assert eF.max() <= 1e-9 and eJ.max() <= 1e-9
+
+
 def test_irregular_force_rejects_bad_entries_on_the_device():
     import torch
     w = inputs.config1()

@@ -331,3 +331,46 @@ def test_exact_boundary_pair_is_regular():
     v2 = np.array([[0.0, 0, 0], [1.0, 0, 0], [0.0, 0, 0]])
     o = oracle.regular(x, v2, m, [0], [0.5], dtr=[0.0], cap=4)
     assert o["nnb"][0] == 1
+
+
+# ------------------------------------------------- conditioning of the sums
+
+@pytest.mark.parametrize("case", range(5))
+def test_term_length_sums_of_a_single_source_are_its_force_and_jerk(case):
+    """With one regular source the length sums are the lengths of the force
+    and jerk themselves (hand-derived closed forms of tests/golden); inside
+    the sphere the source is not counted.  Catches a wrong power of r or a
+    jerk term that differs from the regular sum's."""
+    m_j, R, V, F_exp, J_exp = _load_golden()[case]
+    x = np.array([[0.0, 0, 0], R]); v = np.array([[0.0, 0, 0], V])
+    m = np.array([1.0, m_j])
+    SF, SJ = oracle.regular_mag(x, v, m, act=[0], h=[0.0])
+    assert abs(SF[0] - np.linalg.norm(F_exp)) <= 1e-15 * np.linalg.norm(F_exp)
+    assert abs(SJ[0] - np.linalg.norm(J_exp)) <= 1e-14 * max(np.linalg.norm(J_exp), 1e-300)
+    SF, SJ = oracle.regular_mag(x, v, m, act=[0], h=[1.5 * np.linalg.norm(R)])
+    assert SF[0] == 0.0 and SJ[0] == 0.0
+
+
+def test_term_length_sums_see_the_cancellation():
+    """Two equal masses at +-r on the x axis, at rest: the forces cancel
+    (F = 0) while SF = 2 m / r^2; moving with velocity u along y, each jerk
+    term has length m u / r^3 and they add up (J = 2 m u / r^3 = SJ).  Random
+    systems: SF >= |F|, SJ >= |J| with equality only without cancellation."""
+    r, mj, u = 0.75, 0.125, 0.5
+    x = np.array([[0.0, 0, 0], [r, 0, 0], [-r, 0, 0]])
+    v = np.array([[0.0, 0, 0], [0, u, 0], [0, u, 0]])
+    m = np.array([1.0, mj, mj])
+    out = oracle.regular(x, v, m, act=[0], h=[0.0], cap=4)
+    SF, SJ = oracle.regular_mag(x, v, m, act=[0], h=[0.0])
+    assert np.all(out["F"][0] == 0.0)
+    assert SF[0] == 2 * mj / r**2
+    np.testing.assert_allclose(out["J"][0], [0, 2 * mj * u / r**3, 0], rtol=1e-15)
+    assert abs(SJ[0] - 2 * mj * u / r**3) <= 1e-15 * SJ[0]
+    x, v, m = _rand_system(40, seed=5)
+    act = np.arange(40, dtype=np.int32)
+    h = np.full(40, 0.3)
+    out = oracle.regular(x, v, m, act, h, cap=40)
+    SF, SJ = oracle.regular_mag(x, v, m, act, h)
+    assert np.all(SF >= np.linalg.norm(out["F"], axis=1) * (1 - 1e-14))
+    assert np.all(SJ >= np.linalg.norm(out["J"], axis=1) * (1 - 1e-14))
+    assert np.median(SF / np.linalg.norm(out["F"], axis=1)) > 1.0
