@@ -152,8 +152,8 @@ void nb_destroy(nb_ctx *ctx);
  * MIXED and FP32 forms.
  * Velocity frame (no counterpart in the paper): the MIXED and FP32 copies
  * hold v - u, formed in FP64 before rounding, where the frame velocity u is
- * the mean start velocity v0 of 64 particles spread evenly over this call's
- * range (all of them if n < 64), computed on the device inside the same
+ * the mean start velocity v0 of 32 particles spread evenly over this call's
+ * range (all of them if n < 32), computed on the device inside the same
  * launch; with NB_KEEP_FRAME in `forms` the context's current frame is used
  * instead (the last computed one, or the one given to nb_set_frame).  Only
  * velocity differences enter the results, so u changes no result beyond

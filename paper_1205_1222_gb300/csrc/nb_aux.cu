@@ -67,39 +67,41 @@ __device__ __forceinline__ void write_pairs(float4 *const *streams, const float 
 
 }  // namespace
 
-// Particles sampled for the frame velocity of a prediction.
-constexpr int kFrameSamples = 64;
-
 // Frame velocity of this call: the plain mean of the start velocities of
-// particles floor(k n / S), k = 0 .. S-1 (S = min(n, kFrameSamples)), summed
-// in FP32 in a fixed order (a lane tree per warp, then the warps in order),
-// so every block gets the same bits.  Any velocity near the cluster's bulk
-// motion serves; the mean of a sample is one within about a dispersion / 8.
-// All threads of the block must call it.
-__device__ void frame_velocity(const PredParams &p, double (&u)[3])
+// particles floor(k n / S), k = 0 .. S-1 (S = min(n, 32): lane k loads one),
+// summed in FP32 over an xor butterfly of the lanes, so every lane of every
+// warp gets the same bits (each addition is commutative).  Any velocity near
+// the cluster's bulk motion serves; the mean of the sample is one within
+// about a dispersion / 5.  The sample's loads are issued first and summed
+// after the polynomial, so their latency overlaps the slot's own loads.
+// All lanes of the warp must call both halves.
+struct FrameSample {
+    float s[3];
+};
+
+__device__ __forceinline__ FrameSample frame_sample(const PredParams &p)
 {
-    __shared__ float part[32][3];
+    FrameSample f{{0.f, 0.f, 0.f}};
+    if (p.keep_frame) return f;
+    const int64_t S = p.n < 32 ? p.n : 32;
+    const int64_t k = threadIdx.x & 31;
+    if (k < S) {
+        const int64_t j = k * p.n / S;
+        for (int c = 0; c < 3; c++) f.s[c] = __double2float_rn(p.v0[3 * j + c]);
+    }
+    return f;
+}
+
+__device__ __forceinline__ void frame_velocity(const PredParams &p, FrameSample f, double (&u)[3])
+{
     if (p.keep_frame) {
         for (int c = 0; c < 3; c++) u[c] = p.frame[c];
         return;
     }
-    const int64_t S = p.n < kFrameSamples ? p.n : kFrameSamples;
-    float s[3] = {0.f, 0.f, 0.f};
-    for (int64_t k = threadIdx.x; k < S; k += blockDim.x) {
-        const int64_t j = k * p.n / S;
-        for (int c = 0; c < 3; c++) s[c] += __double2float_rn(p.v0[3 * j + c]);
-    }
+    const int64_t S = p.n < 32 ? p.n : 32;
     for (int o = 16; o > 0; o >>= 1)
-        for (int c = 0; c < 3; c++) s[c] += __shfl_xor_sync(0xffffffffu, s[c], o);
-    const int warp = threadIdx.x >> 5, nw = (blockDim.x + 31) >> 5;
-    if ((threadIdx.x & 31) == 0)
-        for (int c = 0; c < 3; c++) part[warp][c] = s[c];
-    __syncthreads();
-    for (int c = 0; c < 3; c++) {
-        float t = 0.f;
-        for (int w = 0; w < nw; w++) t += part[w][c];
-        u[c] = S > 0 ? static_cast<double>(t / static_cast<float>(S)) : 0.0;
-    }
+        for (int c = 0; c < 3; c++) f.s[c] += __shfl_xor_sync(0xffffffffu, f.s[c], o);
+    for (int c = 0; c < 3; c++) u[c] = S > 0 ? static_cast<double>(f.s[c] / static_cast<float>(S)) : 0.0;
     if (blockIdx.x == 0 && threadIdx.x == 0)
         for (int c = 0; c < 3; c++) p.frame[c] = u[c];
 }
@@ -124,8 +126,7 @@ __device__ __forceinline__ void taylor(const PredParams &p, int64_t j, double (&
 
 __global__ void predict_kernel(const PredParams p)
 {
-    double u[3];
-    frame_velocity(p, u);   // before any thread leaves: it holds a block barrier
+    const FrameSample fs = frame_sample(p);
     const int64_t j = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
     // every lane takes part in the shuffles; lanes past the end only pass values along
     const bool live = j < p.n;
@@ -133,6 +134,8 @@ __global__ void predict_kernel(const PredParams p)
     double x[3] = {0, 0, 0}, v[3] = {0, 0, 0};
     const double m = live ? p.m[j] : 0.0;
     if (live) taylor(p, j, x, v);
+    double u[3];
+    frame_velocity(p, fs, u);
     const int64_t s = p.offset + j;
     if ((p.forms & 1) && live) {
         p.pos64[s] = make_double4_32a(x[0], x[1], x[2], m);

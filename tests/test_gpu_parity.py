@@ -729,7 +729,7 @@ def test_two_float_positions_with_bulk_velocity(bulk):
 
 
 def test_frame_velocity_is_the_sampled_mean_and_matters():
-    """The frame velocity is the mean start velocity of 64 particles spread
+    """The frame velocity is the mean start velocity of 32 particles spread
     evenly over the predicted range; predicting the same moving cluster with
     a zero frame instead (nb_set_frame + NB_KEEP_FRAME: FP32 velocities in the
     caller's frame, as without the frame) loses the jerk tolerance of the
@@ -742,7 +742,7 @@ def test_frame_velocity_is_the_sampled_mean_and_matters():
     with Context(w.n) as ctx:
         d = upload(w)
         ctx.predict(d["x0"], d["v0"], d["a0"], d["adot0"], d["m"], d["t0"], w.t)
-        k = (np.arange(64) * w.n) // 64
+        k = (np.arange(32) * w.n) // 32
         want = w.v0[k].astype(np.float32).astype(np.float64).mean(axis=0)
         got = np.array(B.nb_get_frame(ctx.h))
         assert np.allclose(got, want, rtol=0, atol=1e-4), (got, want)
