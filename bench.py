@@ -176,11 +176,9 @@ def rejected(clk):
 
 # Sources that define the profiled regular-force kernel and its launch: the
 # committed ncu summary's traffic is reported only while these are unchanged.
-# The device code of the profiled kernel and the registry entry that fixes its
-# tiling and shared memory (its launch shape is the tiling the summary names,
-# which profiled_traffic() also checks).
-KERNEL_SOURCES = ("nb_device.cuh", "nb_regf.cuh", "nb_pair_ops.cuh", "nb_regf3.cuh", "nb_regf_ws.cuh",
-                  "nb_kernels.cuh", "nb_kern_mixed.cu")
+# The device code of the profiled kernel (its launch shape is the tiling the
+# summary names, which profiled_traffic() also checks).
+KERNEL_SOURCES = ("nb_device.cuh", "nb_regf.cuh", "nb_pair_ops.cuh", "nb_regf3.cuh", "nb_regf_ws.cuh")
 
 
 def kernel_source_hash():
