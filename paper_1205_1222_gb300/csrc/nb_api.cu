@@ -9,6 +9,7 @@
 #include <cstdio>
 #include <cstring>
 #include <map>
+#include <tuple>
 #include <mutex>
 #include <string>
 #include <vector>
@@ -171,6 +172,11 @@ uint64_t tune_key(int mode, int flags, int act_class, int j_class)
 // criterion (1) and potential (2) bits of a call.
 constexpr int kBatchedClass = 4;
 
+// Tiling code of the thread-block-cluster kernel (nb_regf_cl.cuh) and its
+// largest cluster (non-portable size; every CTA of a cluster sits in one GPC).
+constexpr int kClusterPacked = 20;
+constexpr int kMaxClusterSplits = 16;
+
 // Tiling of a call: the one chosen with nb_set_kernel_config, else the tuned
 // one of the call's size class, else the mode's default.
 nb_kcfg pick_cfg(const nb_ctx *ctx, int mode, int flags, int64_t n_act, int64_t n_j)
@@ -202,6 +208,16 @@ int entry_occupancy(nb_ctx *ctx, int idx, int *occ)
     std::lock_guard<std::mutex> lock(r.mu);
     if (r.occ[idx] < 0) {
         const KernelEntry &e = r.all[idx];
+        if (e.packed == kClusterPacked) {
+            // its list segments grow with the call's cap: allow up to the opt-in limit
+            int optin = 0;
+            NB_CUDA(ctx, cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, ctx->device));
+            NB_CUDA(ctx, cudaFuncSetAttribute(e.fn, cudaFuncAttributeMaxDynamicSharedMemorySize, optin));
+            NB_CUDA(ctx, cudaFuncSetAttribute(e.fn, cudaFuncAttributeNonPortableClusterSizeAllowed, 1));
+            r.occ[idx] = 1;
+            *occ = 1;
+            return NB_OK;
+        }
         NB_CUDA(ctx, cudaFuncSetAttribute(e.fn, cudaFuncAttributeMaxDynamicSharedMemorySize, e.smem));
         int o = 0;
         NB_CUDA(ctx, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o, e.fn, e.warps * 32, e.smem));
@@ -227,6 +243,9 @@ void tile_cluster(const KernelEntry &e, int occ, int sm, const nb_kcfg *cfg, Clu
     int tps;
     if (cfg && cfg->split > 0) {
         tps = cfg->split;
+    } else if (e.packed == kClusterPacked) {
+        // thread-block-cluster kernel: as many splits as fit one cluster
+        tps = std::max(1, (d.n_tiles + kMaxClusterSplits - 1) / kMaxClusterSplits);
     } else if (e.packed < 2) {
         // scalar kernels: enough work items for ~4 resident CTAs' worth of
         // items per slot, but at least two tiles per item
@@ -258,18 +277,19 @@ void tile_cluster(const KernelEntry &e, int occ, int sm, const nb_kcfg *cfg, Clu
     d.n_split = d.n_tiles == 0 ? 1 : (d.n_tiles + d.tiles_per_split - 1) / d.tiles_per_split;
 }
 
-// Bytes of split scratch one cluster needs, and the carving of it.
-size_t cluster_scratch(const ClusterDesc &d)
+// Bytes of split scratch one cluster needs, and the carving of it (the
+// thread-block-cluster kernel keeps its partials in shared memory).
+size_t cluster_scratch(const ClusterDesc &d, int packed = 0)
 {
-    if (d.n_split <= 1) return 0;
+    if (d.n_split <= 1 || packed == kClusterPacked) return 0;
     const size_t cells = static_cast<size_t>(d.n_split) * d.n_act;
     return align_up(cells * 8 * sizeof(double), 256) + align_up(cells * sizeof(int32_t), 256) +
            align_up(cells * static_cast<size_t>(d.cap) * sizeof(int32_t), 256);
 }
 
-void carve_scratch(ClusterDesc &d, char *base)
+void carve_scratch(ClusterDesc &d, char *base, int packed = 0)
 {
-    if (d.n_split <= 1) { d.pF = nullptr; d.pcnt = nullptr; d.plist = nullptr; return; }
+    if (d.n_split <= 1 || packed == kClusterPacked) { d.pF = nullptr; d.pcnt = nullptr; d.plist = nullptr; return; }
     const size_t cells = static_cast<size_t>(d.n_split) * d.n_act;
     d.pF = reinterpret_cast<double *>(base);
     base += align_up(cells * 8 * sizeof(double), 256);
@@ -470,6 +490,117 @@ int sort_and_frames(nb_ctx *ctx, const Call &c, int per_block, ClusterDesc &d, c
     return NB_OK;
 }
 
+// Dynamic shared memory of a kernel launch: the entry's, plus the list
+// segments of the thread-block-cluster kernel.
+size_t launch_smem(const KernelEntry &e, int cap)
+{
+    if (e.packed != kClusterPacked) return static_cast<size_t>(e.smem);
+    return static_cast<size_t>(e.smem) + static_cast<size_t>(iblock_size(e)) * cap * sizeof(int32_t);
+}
+
+// Whether the thread-block-cluster kernel can run a call tiled as d: at most
+// kMaxClusterSplits splits, shared memory within the opt-in limit, and at
+// least one cluster of that size fits the GPU (answers cached per size).
+bool cluster_fits(nb_ctx *ctx, int idx, const ClusterDesc &d)
+{
+    const KernelEntry &e = registry().all[idx];
+    if (d.n_split < 1 || d.n_split > kMaxClusterSplits) return false;
+    int optin = 0;
+    if (cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, ctx->device) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    const size_t smem = launch_smem(e, d.cap);
+    if (smem > static_cast<size_t>(optin)) return false;
+    static std::mutex mu;
+    static std::map<std::tuple<int, int, int, size_t>, bool> known;
+    const auto key = std::make_tuple(ctx->device, idx, static_cast<int>(d.n_split), smem);
+    std::lock_guard<std::mutex> lock(mu);
+    const auto it = known.find(key);
+    if (it != known.end()) return it->second;
+    cudaLaunchConfig_t lc = {};
+    lc.gridDim = dim3(static_cast<unsigned>(d.n_split));
+    lc.blockDim = dim3(e.warps * 32);
+    lc.dynamicSmemBytes = smem;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeClusterDimension;
+    at[0].val.clusterDim.x = static_cast<unsigned>(d.n_split);
+    at[0].val.clusterDim.y = 1;
+    at[0].val.clusterDim.z = 1;
+    lc.attrs = at;
+    lc.numAttrs = 1;
+    int n = 0;
+    const bool ok = cudaOccupancyMaxActiveClusters(&n, e.fn, &lc) == cudaSuccess && n > 0;
+    if (!ok) cudaGetLastError();
+    known[key] = ok;
+    return ok;
+}
+
+// Launch the regular-force kernel of entry e over the work of p: persistent
+// grid of `grid` CTAs, or, for the thread-block-cluster kernel, one cluster of
+// d0.n_split CTAs per block of active particles.
+int launch_regf(nb_ctx *ctx, const KernelEntry &e, const nb::RegfParams &p, int64_t grid, cudaStream_t st)
+{
+    nb::RegfParams q = p;
+    void *args[] = {&q};
+    if (e.packed != kClusterPacked) {
+        NB_CUDA(ctx, cudaLaunchKernel(e.fn, dim3(static_cast<unsigned>(grid)), dim3(e.warps * 32), args, e.smem, st));
+        return NB_OK;
+    }
+    cudaLaunchConfig_t lc = {};
+    lc.gridDim = dim3(static_cast<unsigned>(static_cast<int64_t>(p.d0.n_iblk) * p.d0.n_split));
+    lc.blockDim = dim3(e.warps * 32);
+    lc.dynamicSmemBytes = launch_smem(e, p.d0.cap);
+    lc.stream = st;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeClusterDimension;
+    at[0].val.clusterDim.x = static_cast<unsigned>(p.d0.n_split);
+    at[0].val.clusterDim.y = 1;
+    at[0].val.clusterDim.z = 1;
+    lc.attrs = at;
+    lc.numAttrs = 1;
+    NB_CUDA(ctx, cudaLaunchKernelExC(&lc, e.fn, args));
+    return NB_OK;
+}
+
+// Kernel entry, resident CTAs per SM and tiling of a single call: the
+// configuration chosen (cfg_override, else nb_set_kernel_config, else the
+// tuned one of the call's size class, else the default), moved to a
+// per-particle-layout kernel for a j-range at an odd slot, and to the mode's
+// default when it names the cluster kernel for a split count, cap or cluster
+// size that kernel cannot take.
+int select_single(nb_ctx *ctx, const Call &c, const nb_kcfg *cfg_override, int *idx_out, int *occ_out,
+                  ClusterDesc *d_out)
+{
+    const int flags = (c.dtr ? 1 : 0) | (c.pot ? 2 : 0);
+    nb_kcfg cfg = cfg_override ? *cfg_override : pick_cfg(ctx, c.mode, flags, c.n_act, c.n_j);
+    for (int attempt = 0; attempt < 2; attempt++) {
+        int idx = find_entry(c.mode, cfg, flags);
+        if (idx < 0) { ctx->err = "no kernel for this mode"; return NB_ERR_UNSUPPORTED; }
+        if (registry().all[idx].packed >= 2 && (c.j_begin & 1)) idx = layout_fallback(c.mode, idx, flags);
+        if (registry().all[idx].packed >= 2 && (c.j_begin & 1)) {
+            ctx->err = "no per-particle-layout kernel for a j-range at an odd slot with these flags";
+            return NB_ERR_UNSUPPORTED;
+        }
+        int occ = 0;
+        const int rc = entry_occupancy(ctx, idx, &occ);
+        if (rc != NB_OK) return rc;
+        ClusterDesc d = make_desc(c);
+        tile_cluster(registry().all[idx], occ, ctx->sm_count, &cfg, d);
+        if (registry().all[idx].packed == kClusterPacked && !cluster_fits(ctx, idx, d)) {
+            cfg = default_cfg(c.mode);
+            continue;
+        }
+        d.item_begin = 0;
+        *idx_out = idx;
+        *occ_out = occ;
+        *d_out = d;
+        return NB_OK;
+    }
+    ctx->err = "no kernel for this call";
+    return NB_ERR_UNSUPPORTED;
+}
+
 int run_single(nb_ctx *ctx, const Call &c, const nb_kcfg *cfg_override, cudaStream_t st)
 {
     int rc = check_call(ctx, c);
@@ -477,25 +608,14 @@ int run_single(nb_ctx *ctx, const Call &c, const nb_kcfg *cfg_override, cudaStre
     ctx->last_launches = 0;
     if (c.n_act == 0) return NB_OK;
     DeviceGuard guard(ctx->device);
-    const int flags = (c.dtr ? 1 : 0) | (c.pot ? 2 : 0);
-    const nb_kcfg cfg = cfg_override ? *cfg_override : pick_cfg(ctx, c.mode, flags, c.n_act, c.n_j);
-    int idx = find_entry(c.mode, cfg, flags);
-    if (idx < 0) { ctx->err = "no kernel for this mode"; return NB_ERR_UNSUPPORTED; }
-    if (registry().all[idx].packed >= 2 && (c.j_begin & 1)) idx = layout_fallback(c.mode, idx, flags);
-    if (registry().all[idx].packed >= 2 && (c.j_begin & 1)) {
-        ctx->err = "no per-particle-layout kernel for a j-range at an odd slot with these flags";
-        return NB_ERR_UNSUPPORTED;
-    }
-    int occ = 0;
-    rc = entry_occupancy(ctx, idx, &occ);
+    int idx = -1, occ = 0;
+    ClusterDesc d{};
+    rc = select_single(ctx, c, cfg_override, &idx, &occ, &d);
     if (rc != NB_OK) return rc;
     const KernelEntry &e = registry().all[idx];
-    ClusterDesc d = make_desc(c);
-    tile_cluster(e, occ, ctx->sm_count, &cfg, d);
-    d.item_begin = 0;
-    rc = grow_scratch(ctx, cluster_scratch(d), st);
+    rc = grow_scratch(ctx, cluster_scratch(d, e.packed), st);
     if (rc != NB_OK) return rc;
-    carve_scratch(d, static_cast<char *>(ctx->scratch));
+    carve_scratch(d, static_cast<char *>(ctx->scratch), e.packed);
     int sort_launches = 0;
     if (e.packed == 4) {   // framed kernel: spatial order of the active set and per-block frames
         rc = sort_and_frames(ctx, c, e.warps * e.ipw, d, st);
@@ -515,11 +635,10 @@ int run_single(nb_ctx *ctx, const Call &c, const nb_kcfg *cfg_override, cudaStre
     p.wait_ns = ctx->wait_ns;
     p.extra_tx = ctx->extra_tx;
     const int64_t grid = std::min<int64_t>(p.n_items, static_cast<int64_t>(ctx->sm_count) * occ);
-    void *args[] = {&p};
-    NB_CUDA(ctx, cudaLaunchKernel(e.fn, dim3(static_cast<unsigned>(grid)), dim3(e.warps * 32), args,
-                                  e.smem, st));
+    rc = launch_regf(ctx, e, p, grid, st);
+    if (rc != NB_OK) return rc;
     ctx->last_launches = 1 + sort_launches;
-    if (d.n_split > 1) {
+    if (d.n_split > 1 && e.packed != kClusterPacked) {
         nb::MergeParams mp{};
         mp.d0 = d;
         mp.n_clusters = 1;
@@ -818,7 +937,7 @@ size_t nb_scratch_bytes(nb_ctx *ctx, int64_t n_j, int32_t n_act, int32_t cap, in
         d.n_act = n_act;
         d.cap = cap;
         tile_cluster(registry().all[idx], occ, ctx->sm_count, &cfg, d);
-        best = std::max(best, cluster_scratch(d));
+        best = std::max(best, cluster_scratch(d, registry().all[idx].packed));
     }
     return best;
 }
@@ -992,6 +1111,12 @@ int nb_autotune(nb_ctx *ctx, int64_t j_begin, int64_t n_j, int32_t n_act, const 
             const int tps = sp == 0 ? d.tiles_per_split : sp;
             if (std::find(tried.begin(), tried.end(), tps) != tried.end()) continue;
             tried.push_back(tps);
+            if (e.packed == kClusterPacked) {   // only the splits one cluster can hold
+                ClusterDesc dc = d;
+                const nb_kcfg cc{e.warps, e.ipw, e.jtile, tps, e.packed};
+                tile_cluster(e, occ, ctx->sm_count, &cc, dc);
+                if (!cluster_fits(ctx, static_cast<int>(i), dc)) continue;
+            }
             const nb_kcfg cfg{e.warps, e.ipw, e.jtile, sp, e.packed};
             float ms = 0.f;
             rc = nb_time_regular_force(ctx, &cfg, j_begin, n_j, n_act, act, h, dtr, cap, mode, F, J, pot, nnb,
@@ -1223,6 +1348,8 @@ int nb_plan_create(nb_ctx *ctx, int32_t n_clusters, const nb_cluster *cl, int mo
         cfg = it != ctx->tuned.end() ? it->second.cfg : pick_cfg(ctx, mode, flags, std::max<int64_t>(act_sum, 1), j_max);
     }
     int idx = find_entry(mode, cfg, flags);
+    if (idx >= 0 && registry().all[idx].packed == kClusterPacked)   // serves single calls only
+        idx = find_entry(mode, default_cfg(mode), flags);
     if (idx < 0) return NB_ERR_UNSUPPORTED;
     bool odd = false;
     for (int c = 0; c < n_clusters; c++) odd |= (cl[c].j_begin & 1) != 0;
@@ -1431,6 +1558,7 @@ int nb_plan_autotune(nb_plan *p, int reps, nb_stream_t stream, nb_kcfg *best, fl
         const KernelEntry &e = r.all[i];
         if (e.mode != p->mode || e.flags != p->flags) continue;
         if (e.packed >= 2 && odd) continue;   // j-pair layouts need even first slots
+        if (e.packed == kClusterPacked) continue;   // serves single calls only
         // j-split length in tiles: the plan's heuristic (0), powers of two up
         // to the largest cluster's tile count, and that count (no split)
         const int max_tiles = static_cast<int>((p->j_max + e.jtile - 1) / e.jtile);
@@ -1571,23 +1699,12 @@ extern "C" int nb_regular_force_noalloc(nb_ctx *ctx, int64_t j_begin, int64_t n_
     if (rc != NB_OK) return rc;
     // the tiling nb_regular_force would take: set by nb_set_kernel_config, else
     // the tuned one of the call's size class, else the default
-    const int flags = (c.dtr ? 1 : 0) | (c.pot ? 2 : 0);
-    const nb_kcfg cfg = pick_cfg(ctx, c.mode, flags, c.n_act, c.n_j);
-    int idx = find_entry(c.mode, cfg, flags);
-    if (idx < 0) { ctx->err = "no kernel for this mode"; return NB_ERR_UNSUPPORTED; }
-    if (registry().all[idx].packed >= 2 && (c.j_begin & 1)) idx = layout_fallback(c.mode, idx, flags);
-    if (registry().all[idx].packed >= 2 && (c.j_begin & 1)) {
-        ctx->err = "no per-particle-layout kernel for a j-range at an odd slot with these flags";
-        return NB_ERR_UNSUPPORTED;
-    }
-    int occ = 0;
-    rc = entry_occupancy(ctx, idx, &occ);
+    int idx = -1, occ = 0;
+    ClusterDesc d{};
+    rc = select_single(ctx, c, nullptr, &idx, &occ, &d);
     if (rc != NB_OK) return rc;
     const KernelEntry &e = registry().all[idx];
-    ClusterDesc d = make_desc(c);
-    tile_cluster(e, occ, ctx->sm_count, &cfg, d);
-    d.item_begin = 0;
-    const size_t need = cluster_scratch(d);
+    const size_t need = cluster_scratch(d, e.packed);
     if (need > kNoAllocScratchBytes) {
         ctx->err = "the call needs " + std::to_string(need) + " bytes of split scratch; the fixed array of "
                    "nb_regular_force_noalloc holds " + std::to_string(kNoAllocScratchBytes) +
@@ -1597,7 +1714,7 @@ extern "C" int nb_regular_force_noalloc(nb_ctx *ctx, int64_t j_begin, int64_t n_
     // The array keeps the previous call's contents.  Nothing needs clearing:
     // every work item stores (does not add to) its own (split, particle)
     // partials, count and list slots, and the merge reads only those.
-    carve_scratch(d, static_cast<char *>(scratch));
+    carve_scratch(d, static_cast<char *>(scratch), e.packed);
 
     nb::RegfParams p{};
     p.js = tile_streams(ctx, c.mode, e);
@@ -1609,10 +1726,10 @@ extern "C" int nb_regular_force_noalloc(nb_ctx *ctx, int64_t j_begin, int64_t n_
     p.wait_ns = ctx->wait_ns;
     p.extra_tx = ctx->extra_tx;
     const int64_t grid = std::min<int64_t>(p.n_items, static_cast<int64_t>(ctx->sm_count) * occ);
-    void *args[] = {&p};
-    NB_CUDA(ctx, cudaLaunchKernel(e.fn, dim3(static_cast<unsigned>(grid)), dim3(e.warps * 32), args, e.smem, st));
+    rc = launch_regf(ctx, e, p, grid, st);
+    if (rc != NB_OK) return rc;
     ctx->last_launches = 1;
-    if (d.n_split > 1) {
+    if (d.n_split > 1 && e.packed != kClusterPacked) {
         nb::MergeParams mp{};
         mp.d0 = d;
         mp.n_clusters = 1;

@@ -58,7 +58,8 @@ struct KernelEntry {
     int mode;        // 0 FP64, 1 MIXED, 2 FP32
     int warps, ipw, jtile;
     int flags;       // bit 0: velocity criterion, bit 1: potential
-    int packed;      // 0: scalar kernel (nb_regf.cuh),
+    int packed;      // 20: thread-block-cluster kernel for small calls (nb_regf_cl.cuh);
+                     // 0: scalar kernel (nb_regf.cuh),
                      // 2: f32x2 over j-pairs on the pair-interleaved streams (nb_regf3.cuh),
                      // 3: as 2 with two j-pairs per lane per step; 4: framed; 5: two-float
                      // positions with FP32 velocity differences; 5 + NL / 10 + NL: the

@@ -13,6 +13,7 @@ static const KernelEntry g_fp32[] = {
     NB_KERNEL_ENTRY3(PairFP32, 2, 16, 2, 512, 4, 1, 0, 1),
     NB_KERNEL_ENTRY3(PairFP32, 2, 16, 2, 512, 4, 2, 0, 1),
     NB_KERNEL_ENTRY3(PairFP32, 2, 8, 4, 512, 4, 1, 0, 1),
+    NB_KERNEL_ENTRY_CL(PairFP32, 2, 8, 2, 1024, 0),   // cluster kernel for small calls
     NB_KERNEL_ENTRY(FormFP32, 2, 8, 4, 512, 0),
     NB_KERNEL_ENTRY(FormFP32, 2, 8, 8, 512, 0),
     NB_KERNEL_ENTRY(FormFP32, 2, 8, 2, 512, 0),

@@ -5,6 +5,7 @@
 #include "nb_regf.cuh"
 #include "nb_regf3.cuh"
 #include "nb_regf_ws.cuh"
+#include "nb_regf_cl.cuh"
 
 #define NB_KERNEL_ENTRY(FORM, MODE, W, I, JT, FL)                                       \
     {                                                                                   \
@@ -44,6 +45,16 @@
         1, (WC) + (NL), I, JT, FL, 10 + (NL),                                           \
             reinterpret_cast<const void *>(&nb::regf3ws_kernel<nb::PairMixed, WC, NL, I, JT, NST, FL>), \
             nb::ws_smem_bytes<nb::PairMixed, WC, NL, I, JT, NST>(((FL) & 2) != 0), NL  \
+    }
+
+// Thread-block-cluster kernel for small calls (packed = 20): the j-splits of
+// a block of active particles are the CTAs of one cluster and reduce through
+// distributed shared memory.  smem is the size without the list segments
+// (those add W * I * cap * 4 bytes at launch).
+#define NB_KERNEL_ENTRY_CL(FORM, MODE, W, I, JT, FL)                                    \
+    {                                                                                   \
+        MODE, W, I, JT, FL, 20, reinterpret_cast<const void *>(&nb::regf_cl_kernel<FORM, W, I, JT, FL>), \
+            nb::ClLayout<FORM, W, I, JT>::bytes(((FL) & 2) != 0, 0)                     \
     }
 
 // Framed two-float kernel (packed = 4): compact blocks of the spatially sorted

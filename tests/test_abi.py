@@ -45,7 +45,7 @@ def test_library_loads_and_answers_host_queries(lib_path):
         assert len(set(cfgs)) == n
         for w, ipw, jt, split, packed in cfgs:
             assert w > 0 and ipw > 0 and jt % 32 == 0 and split == 0
-            assert packed in ((0,) if mode == binding.NB_FP64 else (0, 2, 3, 4, 5, 6, 7, 8, 9, 11, 12, 13, 14))
+            assert packed in ((0,) if mode == binding.NB_FP64 else (0, 2, 3, 4, 5, 6, 7, 8, 9, 11, 12, 13, 14, 20))
     assert lib.nb_create is not None
 
 
