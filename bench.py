@@ -178,7 +178,8 @@ def rejected(clk):
 # committed ncu summary's traffic is reported only while these are unchanged.
 # The device code of the profiled kernel (its launch shape is the tiling the
 # summary names, which profiled_traffic() also checks).
-KERNEL_SOURCES = ("nb_device.cuh", "nb_regf.cuh", "nb_pair_ops.cuh", "nb_regf3.cuh", "nb_regf_ws.cuh")
+KERNEL_SOURCES = ("nb_device.cuh", "nb_regf.cuh", "nb_pair_ops.cuh", "nb_regf3.cuh", "nb_regf_ws.cuh",
+                  "nb_kernels.cuh")
 
 
 def kernel_source_hash():

@@ -85,9 +85,9 @@ __device__ __forceinline__ FrameSample frame_sample(const PredParams &p)
     if (p.keep_frame) return f;
     const int64_t S = p.n < 32 ? p.n : 32;
     const int64_t k = threadIdx.x & 31;
-    if (k < S) {
+    if (k < S) {   // every warp reads the same 32 records: through the read-only (L1) path
         const int64_t j = k * p.n / S;
-        for (int c = 0; c < 3; c++) f.s[c] = __double2float_rn(p.v0[3 * j + c]);
+        for (int c = 0; c < 3; c++) f.s[c] = __double2float_rn(__ldg(p.v0 + 3 * j + c));
     }
     return f;
 }

@@ -29,13 +29,13 @@
             nb::pair_smem_bytes<nb::PairMixedX, W, I, JT, NST>(((FL) & 2) != 0)        \
     }
 
-// j-pair kernel with WC compute warps and NL list warps (packed = 5 + NL); the
-// entry's warps field is the CTA's total (WC + NL).
+// j-pair kernel with WC compute warps and NL list warps (packed = 5 + NL) and
+// a four-slot flag ring; the entry's warps field is the CTA's total (WC + NL).
 #define NB_KERNEL_ENTRY6(FORM, MODE, WC, NL, I, JT, NST, FL)                            \
     {                                                                                   \
         MODE, (WC) + (NL), I, JT, FL, 5 + (NL),                                         \
-            reinterpret_cast<const void *>(&nb::regf3ws_kernel<FORM, WC, NL, I, JT, NST, FL>), \
-            nb::ws_smem_bytes<FORM, WC, NL, I, JT, NST>(((FL) & 2) != 0), NL           \
+            reinterpret_cast<const void *>(&nb::regf3ws_kernel<FORM, WC, NL, I, JT, NST, FL, 4>), \
+            nb::ws_smem_bytes<FORM, WC, NL, I, JT, NST, 4>(((FL) & 2) != 0), NL        \
     }
 
 // The exact pair form (two-float position and velocity differences) with NL

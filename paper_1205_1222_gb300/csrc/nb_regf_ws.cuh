@@ -41,17 +41,19 @@ struct WsLayout {
     }
 };
 
-template <class Fm, int WC, int NL, int I, int JT, int NST>
+template <class Fm, int WC, int NL, int I, int JT, int NST, int FR = 2>
 constexpr int ws_smem_bytes(bool pot)
 {
-    return WsLayout<Fm, WC, NL, I, JT, NST>::bytes(pot);
+    return WsLayout<Fm, WC, NL, I, JT, NST, FR>::bytes(pot);
 }
 
-template <class Fm, int WC, int NL, int I, int JT, int NSTAGE, int FLAGS>
+// FR_: slots of the flag ring between the compute and the list warps (a
+// compute warp is at most FR_ tiles ahead of the list warps).
+template <class Fm, int WC, int NL, int I, int JT, int NSTAGE, int FLAGS, int FR_ = 2>
 __global__ void __launch_bounds__((WC + NL) * 32, 1) regf3ws_kernel(const RegfParams p)
 {
     static_assert(WC % NL == 0, "each list warp serves the same number of compute warps");
-    using L = WsLayout<Fm, WC, NL, I, JT, NSTAGE>;
+    using L = WsLayout<Fm, WC, NL, I, JT, NSTAGE, FR_>;
     using P = Fm;
     using JP = typename P::JP;
     using IB = typename P::IB;
