@@ -30,6 +30,9 @@ static const KernelEntry g_mixed[] = {
     NB_KERNEL_ENTRY_CL(PairMixedX, 1, 8, 2, 1024, 0),   // cluster kernels for small calls
     NB_KERNEL_ENTRY_CL(PairMixedX, 1, 16, 2, 1024, 0),
     NB_KERNEL_ENTRY_CL(PairMixedX, 1, 8, 2, 512, 0),
+    NB_KERNEL_ENTRY_CL(PairMixedX, 1, 8, 1, 1024, 0),   // 8 particles per block: half the work per CTA
+    NB_KERNEL_ENTRY_CL(PairMixedX, 1, 16, 1, 1024, 0),
+    NB_KERNEL_ENTRY_CL(PairMixedX, 1, 4, 2, 1024, 0),
     NB_KERNEL_ENTRY4(16, 2, 512, 4, 1, 0, 1),
     NB_KERNEL_ENTRY4(16, 2, 512, 4, 1, 2, 1),
     NB_KERNEL_ENTRY4(12, 2, 512, 4, 1, 0, 1),
