@@ -9,6 +9,7 @@
 #include <cstdio>
 #include <cstring>
 #include <map>
+#include <queue>
 #include <tuple>
 #include <mutex>
 #include <string>
@@ -117,7 +118,8 @@ struct nb_plan {
     int64_t n_items = 0;
     std::vector<ClusterDesc> descs;
     ClusterDesc *d_table = nullptr;
-    int64_t *d_item_begin = nullptr;
+    int64_t n_slots = 0;                  // slots of the work list (grid x the most items of a CTA)
+    int4 *d_work = nullptr;               // [n_slots] (cluster, i-block, j-split, 0); cluster -1: empty
     int n_merge = 0;
     int64_t merge_total = 0;
     int64_t *d_act_begin = nullptr;
@@ -628,7 +630,7 @@ int run_single(nb_ctx *ctx, const Call &c, const nb_kcfg *cfg_override, cudaStre
     p.soa = jset(ctx, c.mode);
     p.d0 = d;
     p.table = nullptr;
-    p.item_begin = nullptr;
+    p.work = nullptr;
     p.n_clusters = 1;
     p.n_items = static_cast<int64_t>(d.n_iblk) * d.n_split;
     p.status = ctx->d_status;
@@ -1312,7 +1314,7 @@ void nb_plan_destroy(nb_plan *p)
     DeviceGuard guard(p->ctx->device);
     if (p->exec) cudaGraphExecDestroy(p->exec);
     if (p->graph) cudaGraphDestroy(p->graph);
-    void *bufs[] = {p->d_table, p->d_item_begin, p->d_act_begin, p->d_cluster_of, p->scratch};
+    void *bufs[] = {p->d_table, p->d_work, p->d_act_begin, p->d_cluster_of, p->scratch};
     for (void *b : bufs)
         if (b) cudaFree(b);
     delete p;
@@ -1373,12 +1375,9 @@ int nb_plan_create(nb_ctx *ctx, int32_t n_clusters, const nb_cluster *cl, int mo
     p->j_max = j_max;
     // Tile every cluster.  Splits are chosen for the whole batch: the number
     // of work items across clusters should cover the resident CTA slots.
-    // The persistent kernel deals items to its CTAs round-robin (CTA k takes
-    // items k, k + grid, ...), so the clusters are laid out by decreasing
-    // j-tile count: each round of items then costs about the same on every CTA
-    // (for 64 clusters of 1024 .. 32768 particles the slowest CTA's share falls
-    // from 8 % to under 2 % above the mean).  The order only schedules: every
-    // cluster keeps its own output pointers.
+    // The clusters are laid out by decreasing j-tile count (the order of equal
+    // items in the work list below); every cluster keeps its own output
+    // pointers.
     std::vector<int> order(n_clusters);
     for (int c = 0; c < n_clusters; c++) order[c] = c;
     const int64_t jt = p->e->jtile;
@@ -1414,19 +1413,58 @@ int nb_plan_create(nb_ctx *ctx, int32_t n_clusters, const nb_cluster *cl, int mo
     }
     p->n_items = items;
     p->grid = static_cast<int>(std::min<int64_t>(std::max<int64_t>(items, 1), slots));
+    // The work list: the items are dealt to the grid's CTAs longest first,
+    // each to the CTA with the least work so far (LPT); an item costs its
+    // j-tiles plus one for its start and end, which take about one tile's
+    // time.  CTA b runs slots b, b + grid, ... of the list; a CTA with fewer
+    // items than the most loaded one leaves its last slots empty.
+    std::vector<int4> work;
+    {
+        struct Item { int32_t cl, ib, sp, tiles; };
+        std::vector<Item> its;
+        its.reserve(static_cast<size_t>(items));
+        for (int c = 0; c < static_cast<int>(ds.size()); c++) {
+            const ClusterDesc &d = ds[c];
+            for (int ib = 0; ib < d.n_iblk; ib++)
+                for (int sp = 0; sp < d.n_split; sp++) {
+                    const int tb = sp * d.tiles_per_split;
+                    its.push_back({c, ib, sp, std::max(0, std::min(d.tiles_per_split, d.n_tiles - tb))});
+                }
+        }
+        std::stable_sort(its.begin(), its.end(), [](const Item &a, const Item &b) { return a.tiles > b.tiles; });
+        const int G = p->grid;
+        std::vector<std::vector<int32_t>> per(G);
+        using Load = std::pair<int64_t, int>;   // (cost so far, CTA): ties go to the lower CTA
+        std::priority_queue<Load, std::vector<Load>, std::greater<Load>> heap;
+        for (int b = 0; b < G; b++) heap.push({0, b});
+        for (size_t k = 0; k < its.size(); k++) {
+            const Load l = heap.top();
+            heap.pop();
+            per[l.second].push_back(static_cast<int32_t>(k));
+            heap.push({l.first + its[k].tiles + 1, l.second});
+        }
+        size_t most = 0;
+        for (const auto &v : per) most = std::max(most, v.size());
+        p->n_slots = static_cast<int64_t>(most) * G;
+        work.assign(static_cast<size_t>(std::max<int64_t>(p->n_slots, 1)), make_int4(-1, 0, 0, 0));
+        for (int b = 0; b < G; b++)
+            for (size_t k = 0; k < per[b].size(); k++) {
+                const Item &it = its[per[b][k]];
+                work[k * G + b] = make_int4(it.cl, it.ib, it.sp, 0);
+            }
+    }
     auto fail = [&](int code) { nb_plan_destroy(p); return code; };
     if (scratch > 0) {
         if (cudaMalloc(&p->scratch, scratch) != cudaSuccess) { cudaGetLastError(); return fail(NB_ERR_NOMEM); }
     }
     char *base = static_cast<char *>(p->scratch);
-    std::vector<int64_t> item_begin, act_begin;
+    std::vector<int64_t> act_begin;
     std::vector<int32_t> cluster_of;
     int64_t merged = 0;
     for (int c = 0; c < n_clusters; c++) {
         ClusterDesc &d = ds[c];
         carve_scratch(d, base);
         base += cluster_scratch(d);
-        item_begin.push_back(d.item_begin);
         if (d.n_split > 1 && d.n_act > 0) {
             act_begin.push_back(merged);
             cluster_of.push_back(c);
@@ -1436,12 +1474,12 @@ int nb_plan_create(nb_ctx *ctx, int32_t n_clusters, const nb_cluster *cl, int mo
     p->n_merge = static_cast<int>(cluster_of.size());
     p->merge_total = merged;
     if (cudaMalloc(&p->d_table, ds.size() * sizeof(ClusterDesc)) != cudaSuccess ||
-        cudaMalloc(&p->d_item_begin, item_begin.size() * sizeof(int64_t)) != cudaSuccess) {
+        cudaMalloc(&p->d_work, work.size() * sizeof(int4)) != cudaSuccess) {
         cudaGetLastError();
         return fail(NB_ERR_NOMEM);
     }
     if (cudaMemcpy(p->d_table, ds.data(), ds.size() * sizeof(ClusterDesc), cudaMemcpyHostToDevice) != cudaSuccess ||
-        cudaMemcpy(p->d_item_begin, item_begin.data(), item_begin.size() * sizeof(int64_t),
+        cudaMemcpy(p->d_work, work.data(), work.size() * sizeof(int4),
                    cudaMemcpyHostToDevice) != cudaSuccess)
         return fail(NB_ERR_CUDA);
     if (p->n_merge > 0) {
@@ -1474,9 +1512,9 @@ int nb_plan_run(nb_plan *p, nb_stream_t stream)
         rp.js = tile_streams(ctx, p->mode, *p->e);
         rp.soa = jset(ctx, p->mode);
         rp.table = p->d_table;
-        rp.item_begin = p->d_item_begin;
+        rp.work = p->d_work;
         rp.n_clusters = static_cast<int32_t>(p->descs.size());
-        rp.n_items = p->n_items;
+        rp.n_items = p->n_slots;
         rp.status = ctx->d_status;
         rp.wait_ns = ctx->wait_ns;
         rp.extra_tx = ctx->extra_tx;

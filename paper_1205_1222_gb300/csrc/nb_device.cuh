@@ -55,16 +55,37 @@ struct ClusterDesc {
 struct RegfParams {
     JSet js;                      // streams the j-tiles are copied from
     JSet soa;                     // per-particle (SoA) streams of the same form, for the i-values
-    ClusterDesc d0;               // used when table == nullptr
+    ClusterDesc d0;               // used when work == nullptr (a single call)
     const ClusterDesc *table;     // device table of clusters (batched launch)
-    const int64_t *item_begin;    // [n_clusters] copy of table[c].item_begin for the search
+    // batched launch: the work list, one (cluster, i-block, j-split, 0) per
+    // slot (cluster < 0: an empty slot); CTA b takes slots b, b + grid, ...
+    const int4 *work;
     int32_t n_clusters;
-    int64_t n_items;
+    int64_t n_items;              // work items (single call) or slots of the work list
     int *status;
     uint64_t wait_ns;             // bound of every mbarrier wait
     uint32_t extra_tx;            // test hook: bytes expected beyond the copies (0 normally);
                                   // > 0 makes every copy wait run out, exercising the time-out path
 };
+
+// Work item at slot `pos` of the launch: its cluster's table index, i-block
+// and j-split.  A batched launch reads them from the plan's work list (one
+// 16-byte load; false for an empty slot), a single call derives them from
+// the slot number (i-block major, j-split minor).
+__device__ __forceinline__ bool item_at(const RegfParams &p, int64_t pos, int &cl, int &ib, int &sp)
+{
+    if (p.work) {
+        const int4 r = p.work[pos];
+        cl = r.x;
+        ib = r.y;
+        sp = r.z;
+        return cl >= 0;
+    }
+    cl = 0;
+    ib = static_cast<int>(pos / p.d0.n_split);
+    sp = static_cast<int>(pos - static_cast<int64_t>(ib) * p.d0.n_split);
+    return true;
+}
 
 // ------------------------------------------------------------ PTX helpers
 
@@ -237,6 +258,75 @@ __device__ __forceinline__ void write_item_ff(const ClusterDesc &d, int sp, cons
             float2 *slot = reinterpret_cast<float2 *>(d.pF + (static_cast<int64_t>(sp) * d.n_act + ii) * 8);
             slot[c] = make_float2(h, l);
         }
+    }
+}
+
+// Float-float reduce-scatter of V = 8 I values over the 32 lanes of a warp
+// (h[v], l[v]: this lane's part of value v = 8 q + c, component c of particle
+// q as above, zero for c >= NC).  Each of the first log2 V rounds halves what
+// a lane carries: of lanes L and L ^ b (b = 16, 8, ...), the one with bit b
+// set keeps the upper half of the values and the other the lower half, and
+// each adds the half it receives; the remaining rounds add the partner's
+// whole value.  Lane L ends with the total of value L >> (5 - log2 V) in
+// h[0], l[0], with the same bits on every lane that holds it (TwoSum's error
+// term is exact in either operand order).  For V = 16 that is 32 shuffles and
+// 16 float-float additions per lane, against 120 and 60 for a butterfly of
+// every value, and the lanes are left holding one value each for the stores.
+template <int V>
+__device__ __forceinline__ void ff_reduce_scatter(float (&h)[V], float (&l)[V])
+{
+    static_assert(V == 8 || V == 16 || V == 32, "8 components of 1, 2 or 4 particles");
+    constexpr int LV = V == 8 ? 3 : (V == 16 ? 4 : 5);
+    const int lane = threadIdx.x & 31;
+#pragma unroll
+    for (int r = 0; r < LV; r++) {
+        const int m = V >> (r + 1), b = 16 >> r;
+        const bool up = (lane & b) != 0;
+#pragma unroll
+        for (int k = 0; k < m; k++) {
+            const float sh = up ? h[k] : h[k + m], sl = up ? l[k] : l[k + m];
+            float kh = up ? h[k + m] : h[k], kl = up ? l[k + m] : l[k];
+            const float rh = __shfl_xor_sync(0xffffffffu, sh, b);
+            const float rl = __shfl_xor_sync(0xffffffffu, sl, b);
+            ff_add_ff(kh, kl, rh, rl);
+            h[k] = kh;
+            l[k] = kl;
+        }
+    }
+#pragma unroll
+    for (int b = 16 >> LV; b >= 1; b >>= 1) {
+        const float rh = __shfl_xor_sync(0xffffffffu, h[0], b);
+        const float rl = __shfl_xor_sync(0xffffffffu, l[0], b);
+        ff_add_ff(h[0], l[0], rh, rl);
+    }
+}
+
+// The stores of write_item_ff after ff_reduce_scatter: the first lane of
+// each value's lane group stores it.
+template <int I, int NC>
+__device__ __forceinline__ void write_item_rs(const ClusterDesc &d, int sp, float h, float l, const int (&oi)[I],
+                                              int *status)
+{
+    static_assert(NC <= 7, "F, J and the potential");
+    constexpr int SH = I == 1 ? 2 : (I == 2 ? 1 : 0);   // 5 - log2(8 I)
+    const int lane = threadIdx.x & 31;
+    if (lane & ((1 << SH) - 1)) return;
+    const int v = lane >> SH, q = v >> 3, c = v & 7;
+    int i = -1;
+#pragma unroll
+    for (int qq = 0; qq < I; qq++)
+        if (qq == q) i = oi[qq];
+    if (c >= 7 || !row_ok(d, sp, i, status)) return;
+    const int64_t ii = i;
+    if (d.n_split == 1) {
+        if (c >= NC) return;
+        const double x = static_cast<double>(h) + static_cast<double>(l);
+        if (c < 3) d.F[3 * ii + c] = x;
+        else if (c < 6) d.J[3 * ii + c - 3] = x;
+        else if (d.pot) d.pot[ii] = x;
+    } else {
+        float2 *slot = reinterpret_cast<float2 *>(d.pF + (static_cast<int64_t>(sp) * d.n_act + ii) * 8);
+        slot[c] = c < NC ? make_float2(h, l) : make_float2(0.f, 0.f);
     }
 }
 

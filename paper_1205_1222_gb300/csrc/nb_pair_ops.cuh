@@ -112,8 +112,8 @@ __device__ __forceinline__ uint64_t reduce_or_bits(uint64_t b)
 __device__ __forceinline__ int lowest_bit(uint32_t b) { return __ffs(b) - 1; }
 __device__ __forceinline__ int lowest_bit(uint64_t b) { return __ffsll(static_cast<long long>(b)) - 1; }
 
-// Position in the CTA's sequence of j-tiles: the work item, the tile in it,
-// the item's tile end, and the j-range the copies read.
+// Position in the CTA's sequence of j-tiles: the slot of the work item, the
+// tile in it, the item's tile end, and the j-range the copies read.
 struct TileCursor {
     int64_t item;
     int64_t jb;
@@ -122,23 +122,15 @@ struct TileCursor {
 
 __device__ __forceinline__ void cursor_set(const RegfParams &p, TileCursor &c)
 {
+    int cl = 0, ib = 0, sp = 0;
+    for (; c.item < p.n_items; c.item += gridDim.x)   // the consumers skip the same empty slots
+        if (item_at(p, c.item, cl, ib, sp)) break;
     if (c.item >= p.n_items) return;
-    int64_t item_begin, jb;
-    int n_split, tps, n_tiles, nj;
-    if (p.table) {
-        const ClusterDesc &d = p.table[find_cluster(p, c.item)];
-        item_begin = d.item_begin; jb = d.j_begin; nj = d.n_j;
-        n_split = d.n_split; tps = d.tiles_per_split; n_tiles = d.n_tiles;
-    } else {
-        item_begin = p.d0.item_begin; jb = p.d0.j_begin; nj = p.d0.n_j;
-        n_split = p.d0.n_split; tps = p.d0.tiles_per_split; n_tiles = p.d0.n_tiles;
-    }
-    const int64_t local = c.item - item_begin;
-    const int sp = static_cast<int>(local % n_split);
-    c.jb = jb;
-    c.nj = nj;
-    c.tile = sp * tps;
-    c.te = min(c.tile + tps, n_tiles);
+    const ClusterDesc &d = p.work ? p.table[cl] : p.d0;
+    c.jb = d.j_begin;
+    c.nj = d.n_j;
+    c.tile = sp * d.tiles_per_split;
+    c.te = min(c.tile + d.tiles_per_split, d.n_tiles);
 }
 
 __device__ __forceinline__ void cursor_next(const RegfParams &p, TileCursor &c)

@@ -262,16 +262,6 @@ struct FormFP64 {
 
 // ------------------------------------------------------------ the kernel
 
-__device__ __forceinline__ int find_cluster(const RegfParams &p, int64_t item)
-{
-    int lo = 0, hi = p.n_clusters - 1;
-    while (lo < hi) {  // largest c with item_begin[c] <= item
-        const int mid = (lo + hi + 1) >> 1;
-        if (p.item_begin[mid] <= item) lo = mid; else hi = mid - 1;
-    }
-    return lo;
-}
-
 template <class Fm, int JT>
 __device__ __forceinline__ void issue_tile(const RegfParams &p, const ClusterDesc &d, int tile,
                                            uint32_t seq, uint64_t *bar, unsigned char *stages)
@@ -317,12 +307,11 @@ __global__ void __launch_bounds__(W * 32) regf_kernel(const RegfParams p)
     uint32_t issued = 0;   // tiles issued so far (thread 0)
     bool aborted = false;
 
-    for (int64_t item = blockIdx.x; item < p.n_items; item += gridDim.x) {
+    for (int64_t pos = blockIdx.x; pos < p.n_items; pos += gridDim.x) {
+        int cl, ib, sp;
+        if (!item_at(p, pos, cl, ib, sp)) continue;
         ClusterDesc d;
-        if (p.table) d = p.table[find_cluster(p, item)]; else d = p.d0;
-        const int64_t local = item - d.item_begin;
-        const int ib = static_cast<int>(local / d.n_split);
-        const int sp = static_cast<int>(local - static_cast<int64_t>(ib) * d.n_split);
+        if (p.work) d = p.table[cl]; else d = p.d0;
         const int tb = sp * d.tiles_per_split;
         const int te = min(tb + d.tiles_per_split, d.n_tiles);
 
@@ -377,8 +366,9 @@ __global__ void __launch_bounds__(W * 32) regf_kernel(const RegfParams p)
             const int count = min(JT, d.n_j - jt0);
             if (ok) {
                 const bool tailtile = count < JT;
+                const int nsteps = tailtile ? (count + 31) >> 5 : STEPS;   // steps that hold a j
 #pragma unroll 2
-                for (int s = 0; s < STEPS; ++s) {
+                for (int s = 0; s < nsteps; ++s) {
                     const int jl = s * 32 + lane;
                     JS js;
                     Fm::template load_j<JT>(js, st, jl);

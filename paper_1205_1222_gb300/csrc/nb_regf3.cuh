@@ -366,7 +366,7 @@ __device__ __forceinline__ void fence_proxy_async_smem()
 template <class Fm, class Ff, int W, int I, int JT, int NSTAGE, int U, int FLAGS, int MINB>
 __global__ void __launch_bounds__(W * 32, MINB) regf3_kernel(const RegfParams p)
 {
-    static_assert(NSTAGE <= 10, "ring barriers and counters share the first 256 bytes");
+    static_assert(NSTAGE <= 9, "ring barriers, counters and the look-ahead cursor share the first 256 bytes");
     static_assert((JT / 64) % U == 0, "a tile holds a whole number of steps");
     using L = PairLayout<Fm, W, I, JT, NSTAGE>;
     constexpr bool FRAMED = !std::is_same<Ff, NoFrame>::value;
@@ -391,15 +391,15 @@ __global__ void __launch_bounds__(W * 32, MINB) regf3_kernel(const RegfParams p)
     uint64_t *xf = full + NST;                                    // tile rewritten in frame coordinates
     int *rel = reinterpret_cast<int *>(xf + NST);                 // warps done with the stage
     int *claim = rel + NST;                                       // warps that reached the stage
+    // the ring's look-ahead: the tile that the next refill copies (only the
+    // thread that refills a stage reads and advances it)
+    TileCursor *s_la = reinterpret_cast<TileCursor *>(claim + NST);
     unsigned char *stages = smem + L::STAGES;
     float2 *s_tot = reinterpret_cast<float2 *>(smem + L::TOT);
     ListRec *s_rec = reinterpret_cast<ListRec *>(smem + L::rec(POT));
     ClusterDesc *s_d = reinterpret_cast<ClusterDesc *>(smem + L::desc(POT));
 
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-    TileCursor la;
-    la.item = blockIdx.x;
-    cursor_set(p, la);
     if (tid == 0) {
         for (int s = 0; s < NST; s++) {
             mbar_init(&full[s], 1);
@@ -408,13 +408,15 @@ __global__ void __launch_bounds__(W * 32, MINB) regf3_kernel(const RegfParams p)
             claim[s] = 0;
         }
         fence_mbar_init();
-        TileCursor c0 = la;
+        TileCursor c0;
+        c0.item = blockIdx.x;
+        cursor_set(p, c0);
         for (int q = 0; q < NST && c0.item < p.n_items; ++q) {
             issue_pairs<Fm, JT, NST>(p, c0, q, full, stages);
             cursor_next(p, c0);
         }
+        *s_la = c0;   // look-ahead = sequence NST
     }
-    for (int q = 0; q < NST && la.item < p.n_items; ++q) cursor_next(p, la);   // look-ahead = sequence NST
     __syncthreads();
 
     uint32_t g = 0;
@@ -522,8 +524,11 @@ __global__ void __launch_bounds__(W * 32, MINB) regf3_kernel(const RegfParams p)
 #pragma unroll
                 for (int k = 0; k < STEPS / U; ++k) step(k, std::false_type{});
             } else {
+                // the last tile of a j-range: only the steps that hold a j
+                const int whole = count / (U * 64);   // steps with no padding
 #pragma unroll 1
-                for (int k = 0; k < STEPS / U; ++k) step(k, std::true_type{});
+                for (int k = 0; k < whole; ++k) step(k, std::false_type{});
+                if (count - whole * U * 64 > 0) step(whole, std::true_type{});
             }
             // count this warp out of the stage (the list pass below reads only the
             // flags); the last one refills it NST tiles ahead
@@ -531,15 +536,22 @@ __global__ void __launch_bounds__(W * 32, MINB) regf3_kernel(const RegfParams p)
             if (lane == 0) {
                 __threadfence_block();
                 if (atomicAdd(&rel[s], 1) == W - 1) {
+                    // every warp has left the stage, the refiller of the previous
+                    // one among them: its cursor update is visible after the fence
+                    __threadfence_block();
                     rel[s] = 0;
                     if constexpr (FRAMED) {
                         claim[s] = 0;
                         fence_proxy_async_smem();   // the stage was written through the generic proxy
                     }
-                    if (la.item < p.n_items) issue_pairs<Fm, JT, NST>(p, la, g + NST, full, stages);
+                    TileCursor la = *s_la;
+                    if (la.item < p.n_items) {
+                        issue_pairs<Fm, JT, NST>(p, la, g + NST, full, stages);
+                        cursor_next(p, la);
+                        *s_la = la;
+                    }
                 }
             }
-            cursor_next(p, la);
 
             // Neighbour lists of the tile, in ascending j: for each i-particle,
             // the flagged units in order; within a unit the order is (lane, half).
@@ -596,22 +608,18 @@ __global__ void __launch_bounds__(W * 32, MINB) regf3_kernel(const RegfParams p)
         if (aborted) return;
 
         // reduce the float-float totals over the 32 lanes, then write
-        FFKeep<I> kept{};
+        float th[8 * I], tl[8 * I];
 #pragma unroll
         for (int q = 0; q < I; q++) {
 #pragma unroll
-            for (int c = 0; c < NC; c++) {
-                const float2 v = mytot[(q * NC + c) * 32];
-                float hi = v.x, lo = v.y;
-                for (int o = 16; o > 0; o >>= 1) {
-                    const float h2 = __shfl_xor_sync(0xffffffffu, hi, o);
-                    const float l2 = __shfl_xor_sync(0xffffffffu, lo, o);
-                    ff_add_ff(hi, lo, h2, l2);
-                }
-                ff_keep(kept, q, c, hi, lo);
+            for (int c = 0; c < 8; c++) {
+                const float2 v = c < NC ? mytot[(q * NC + c) * 32] : make_float2(0.f, 0.f);
+                th[8 * q + c] = v.x;
+                tl[8 * q + c] = v.y;
             }
         }
-        write_item_ff<I, NC>(d, sp, kept, oidx, p.status);
+        ff_reduce_scatter<8 * I>(th, tl);
+        write_item_rs<I, NC>(d, sp, th[0], tl[0], oidx, p.status);
 #pragma unroll
         for (int q = 0; q < I; q++) {
             const int64_t i = oidx[q];
@@ -628,12 +636,11 @@ __global__ void __launch_bounds__(W * 32, MINB) regf3_kernel(const RegfParams p)
         __syncwarp();
     };
 
-    for (int64_t item = blockIdx.x; item < p.n_items && !aborted; item += gridDim.x) {
-        if (lane == 0) d = p.table ? p.table[find_cluster(p, item)] : p.d0;
+    for (int64_t pos = blockIdx.x; pos < p.n_items && !aborted; pos += gridDim.x) {
+        int cl, ib, sp;
+        if (!item_at(p, pos, cl, ib, sp)) continue;
+        if (lane == 0) d = p.work ? p.table[cl] : p.d0;
         __syncwarp();
-        const int64_t local = item - d.item_begin;
-        const int ib = static_cast<int>(local / d.n_split);
-        const int sp = static_cast<int>(local - static_cast<int64_t>(ib) * d.n_split);
         Frame2 fr{};
         bool framed_item = false;
         if constexpr (FRAMED) {

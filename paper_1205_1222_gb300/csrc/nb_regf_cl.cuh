@@ -189,8 +189,11 @@ __global__ void __launch_bounds__(W * 32, 1) regf_cl_kernel(const RegfParams p)
 #pragma unroll
             for (int k = 0; k < STEPS; ++k) step(k, std::false_type{});
         } else {
+            // the last tile of the j-range: only the steps that hold a j
+            const int whole = count >> 6;   // steps of 64 j with no padding
 #pragma unroll 1
-            for (int k = 0; k < STEPS; ++k) step(k, std::true_type{});
+            for (int k = 0; k < whole; ++k) step(k, std::false_type{});
+            if (count & 63) step(whole, std::true_type{});
         }
         __syncthreads();   // every warp is done with tile t
         if (t + 1 < te) issue_tile(t + 1);
@@ -242,26 +245,25 @@ __global__ void __launch_bounds__(W * 32, 1) regf_cl_kernel(const RegfParams p)
         }
     }
 
-    // this split's float-float partials and counts, in shared memory
+    // this split's float-float partials (component c of particle q at
+    // s_part[(warp I + q) 8 + c], zero for c >= NC) and counts, in shared memory
+    {
+        float th[8 * I], tl[8 * I];
 #pragma unroll
-    for (int q = 0; q < I; q++) {
-        const int ql = warp * I + q;
+        for (int q = 0; q < I; q++) {
 #pragma unroll
-        for (int c = 0; c < 8; c++) {
-            float hi = 0.f, lo = 0.f;
-            if (c < NC) {
-                const float2 v = mytot[(q * NC + c) * 32];
-                hi = v.x;
-                lo = v.y;
-                for (int o = 16; o > 0; o >>= 1) {
-                    const float h2 = __shfl_xor_sync(0xffffffffu, hi, o);
-                    const float l2 = __shfl_xor_sync(0xffffffffu, lo, o);
-                    ff_add_ff(hi, lo, h2, l2);
-                }
+            for (int c = 0; c < 8; c++) {
+                const float2 v = c < NC ? mytot[(q * NC + c) * 32] : make_float2(0.f, 0.f);
+                th[8 * q + c] = v.x;
+                tl[8 * q + c] = v.y;
             }
-            if (lane == 0) s_part[ql * 8 + c] = make_float2(hi, lo);
         }
-        if (lane == 0) s_cnt[ql] = cnt[q];
+        ff_reduce_scatter<8 * I>(th, tl);
+        constexpr int SH = I == 1 ? 2 : (I == 2 ? 1 : 0);   // lane L holds value L >> SH
+        if ((lane & ((1 << SH) - 1)) == 0) s_part[warp * I * 8 + (lane >> SH)] = make_float2(th[0], tl[0]);
+#pragma unroll
+        for (int q = 0; q < I; q++)
+            if (lane == 0) s_cnt[warp * I + q] = cnt[q];
     }
 
     cluster_barrier();
@@ -271,7 +273,7 @@ __global__ void __launch_bounds__(W * 32, 1) regf_cl_kernel(const RegfParams p)
     for (int ql = sp + S * warp; ql < IPB; ql += S * W) {
         const int slot_i = ib * IPB + ql;
         if (slot_i >= d.n_act) continue;
-        float sh[7] = {0, 0, 0, 0, 0, 0, 0}, sl[7] = {0, 0, 0, 0, 0, 0, 0};
+        float sh[8] = {0, 0, 0, 0, 0, 0, 0, 0}, sl[8] = {0, 0, 0, 0, 0, 0, 0, 0};
         int c_s = 0;
         if (lane < S) {
             c_s = ld_peer_s32(peer_addr(s_cnt + ql, lane));
@@ -283,13 +285,7 @@ __global__ void __launch_bounds__(W * 32, 1) regf_cl_kernel(const RegfParams p)
                 sl[c] = v.y;
             }
         }
-        for (int o = 16; o > 0; o >>= 1)
-#pragma unroll
-            for (int c = 0; c < 7; c++) {
-                const float h2 = __shfl_xor_sync(0xffffffffu, sh[c], o);
-                const float l2 = __shfl_xor_sync(0xffffffffu, sl[c], o);
-                ff_add_ff(sh[c], sl[c], h2, l2);
-            }
+        ff_reduce_scatter<8>(sh, sl);   // lane L: component L >> 2 summed over the splits
         // list segments in split order: exclusive prefix of the counts
         int incl = c_s;
         for (int o = 1; o < 32; o <<= 1) {
@@ -316,18 +312,17 @@ __global__ void __launch_bounds__(W * 32, 1) regf_cl_kernel(const RegfParams p)
                     atomicOr(p.status, DEV_BOUNDS);
             }
         }
-        float h = 0.f, l = 0.f;
-#pragma unroll
-        for (int c = 0; c < 7; c++)
-            if (c == lane) { h = sh[c]; l = sl[c]; }
-        const double v = static_cast<double>(h) + static_cast<double>(l);
+        const double v = static_cast<double>(sh[0]) + static_cast<double>(sl[0]);
         const int64_t i = slot_i;
         const int a = d.act[slot_i];
         const double hv = d.h[slot_i];
+        const int c = lane >> 2;
         if (a >= 0 && a < d.n_j && hv >= 0.0 && hv <= DBL_MAX) {
-            if (lane < 3) d.F[3 * i + lane] = v;
-            else if (lane < 6) d.J[3 * i + lane - 3] = v;
-            else if (lane == 6 && POT && d.pot) d.pot[i] = v;
+            if ((lane & 3) == 0) {
+                if (c < 3) d.F[3 * i + c] = v;
+                else if (c < 6) d.J[3 * i + c - 3] = v;
+                else if (c == 6 && POT && d.pot) d.pot[i] = v;
+            }
             if (lane == 0) {
                 d.nnb[i] = total;
                 d.ovf[i] = total > cap ? 1 : 0;

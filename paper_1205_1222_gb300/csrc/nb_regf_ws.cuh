@@ -71,6 +71,7 @@ __global__ void __launch_bounds__((WC + NL) * 32, 1) regf3ws_kernel(const RegfPa
     static_assert(sizeof(Bits) == L::FLB, "flag words");
     static_assert(16 * NST + 16 * FR <= L::HDR, "barriers fit the header");
     constexpr int NCW = WC / NL;                                  // compute warps per list warp
+    static_assert(I * NC <= 32, "one lane per (particle, component) at the end of an item");
 
     extern __shared__ __align__(128) unsigned char smem[];
     uint64_t *full = reinterpret_cast<uint64_t *>(smem);          // tile landed (TMA)
@@ -114,12 +115,11 @@ __global__ void __launch_bounds__((WC + NL) * 32, 1) regf3ws_kernel(const RegfPa
     if (!lister) {
         // ------------------------------------------------------------ compute warps
         float2 *mytot = s_tot + warp * I * NC * 32 + lane;   // + (i * NC + comp) * 32: (hi, lo)
-        for (int64_t item = blockIdx.x; item < p.n_items && !aborted; item += gridDim.x) {
-            if (lane == 0) d = p.table ? p.table[find_cluster(p, item)] : p.d0;
+        for (int64_t pos = blockIdx.x; pos < p.n_items && !aborted; pos += gridDim.x) {
+            int cl, ib, sp;
+            if (!item_at(p, pos, cl, ib, sp)) continue;
+            if (lane == 0) d = p.work ? p.table[cl] : p.d0;
             __syncwarp();
-            const int64_t local = item - d.item_begin;
-            const int ib = static_cast<int>(local / d.n_split);
-            const int sp = static_cast<int>(local - static_cast<int64_t>(ib) * d.n_split);
             const int tb = sp * d.tiles_per_split;
             const int te = min(tb + d.tiles_per_split, d.n_tiles);
             IB ipart[I];
@@ -177,8 +177,11 @@ __global__ void __launch_bounds__((WC + NL) * 32, 1) regf3ws_kernel(const RegfPa
 #pragma unroll
                     for (int k = 0; k < STEPS; ++k) step(k, std::false_type{});
                 } else {
+                    // the last tile of a j-range: only the steps that hold a j
+                    const int whole = count >> 6;   // steps of 64 j with no padding
 #pragma unroll 1
-                    for (int k = 0; k < STEPS; ++k) step(k, std::true_type{});
+                    for (int k = 0; k < whole; ++k) step(k, std::false_type{});
+                    if (count & 63) step(whole, std::true_type{});
                 }
                 // this warp is done with the stage; list warp 0 refills it
                 __syncwarp();
@@ -217,36 +220,78 @@ __global__ void __launch_bounds__((WC + NL) * 32, 1) regf3ws_kernel(const RegfPa
             }
             if (aborted) break;
 
-            // reduce the float-float totals over the 32 lanes, then write F, J (and
-            // the potential); the list warps write the counts and lists
-            // (This kernel serves the large calls: its FP64 conversions on every
-            // lane cost little per item there, and the per-lane store of the
-            // other kernels changed its register allocation for the worse.)
+            // Reduce the float-float totals over the 32 lanes (a butterfly per
+            // value), then write F, J and the potential; the list warps write
+            // the counts and lists.  The two-float forms keep component c of
+            // particle q on lane q NC + c after the butterflies: one FP64
+            // conversion per lane instead of one per value on every lane (the
+            // FP64 pipe is narrow; 0.6 % of the step at N = n_act = 131072, 2.4 %
+            // at 16384 active, 2.5 % for the exact pair form), and a split slot
+            // takes the float-float pair itself.  The plain FP32 form keeps the
+            // all-lane conversion, which left its register allocation without
+            // spills (the per-lane store cost that form 2.6 %).  A reduce-scatter
+            // of the values, cheaper in shuffles, made the pair-term loop slower.
+            if constexpr (!std::is_same<Fm, PairFP32>::value) {
+                float vh = 0.f, vl = 0.f;
 #pragma unroll
-            for (int q = 0; q < I; q++) {
-                double out[7] = {0, 0, 0, 0, 0, 0, 0};
-                for (int c = 0; c < NC; c++) {
-                    const float2 v = mytot[(q * NC + c) * 32];
-                    float hi = v.x, lo = v.y;
-                    for (int o = 16; o > 0; o >>= 1) {
-                        const float h2 = __shfl_xor_sync(0xffffffffu, hi, o);
-                        const float l2 = __shfl_xor_sync(0xffffffffu, lo, o);
-                        ff_add_ff(hi, lo, h2, l2);
+                for (int q = 0; q < I; q++) {
+#pragma unroll
+                    for (int c = 0; c < NC; c++) {
+                        const float2 v = mytot[(q * NC + c) * 32];
+                        float hi = v.x, lo = v.y;
+                        for (int o = 16; o > 0; o >>= 1) {
+                            const float h2 = __shfl_xor_sync(0xffffffffu, hi, o);
+                            const float l2 = __shfl_xor_sync(0xffffffffu, lo, o);
+                            ff_add_ff(hi, lo, h2, l2);
+                        }
+                        if (lane == q * NC + c) { vh = hi; vl = lo; }
                     }
-                    out[c] = static_cast<double>(hi) + static_cast<double>(lo);
                 }
-                const int64_t i = oidx[q];
-                if (lane == 0 && row_ok(d, sp, i, p.status)) {
+                const int q = lane / NC, c = lane - (lane / NC) * NC;
+                int64_t i = -1;
+#pragma unroll
+                for (int qq = 0; qq < I; qq++)
+                    if (qq == q) i = oidx[qq];
+                if (lane < I * NC && row_ok(d, sp, i, p.status)) {
                     if (d.n_split == 1) {
-                        for (int c = 0; c < 3; c++) { d.F[3 * i + c] = out[c]; d.J[3 * i + c] = out[3 + c]; }
-                        if (POT && d.pot) d.pot[i] = out[6];
+                        const double v = static_cast<double>(vh) + static_cast<double>(vl);
+                        if (c < 3) d.F[3 * i + c] = v;
+                        else if (c < 6) d.J[3 * i + c - 3] = v;
+                        else if (d.pot) d.pot[i] = v;
                     } else {
-                        // the split slot holds float-float pairs, as written by write_item_ff
                         float2 *o8 = reinterpret_cast<float2 *>(d.pF + (static_cast<int64_t>(sp) * d.n_act + i) * 8);
-                        for (int c = 0; c < 7; c++) {
-                            const float h = c < NC ? __double2float_rn(out[c]) : 0.f;
-                            const float l = c < NC ? __double2float_rn(out[c] - static_cast<double>(h)) : 0.f;
-                            o8[c] = make_float2(h, l);
+                        o8[c] = make_float2(vh, vl);
+                        if (c == NC - 1)
+                            for (int cc = NC; cc < 7; cc++) o8[cc] = make_float2(0.f, 0.f);
+                    }
+                }
+            } else {
+#pragma unroll
+                for (int q = 0; q < I; q++) {
+                    double out[7] = {0, 0, 0, 0, 0, 0, 0};
+                    for (int c = 0; c < NC; c++) {
+                        const float2 v = mytot[(q * NC + c) * 32];
+                        float hi = v.x, lo = v.y;
+                        for (int o = 16; o > 0; o >>= 1) {
+                            const float h2 = __shfl_xor_sync(0xffffffffu, hi, o);
+                            const float l2 = __shfl_xor_sync(0xffffffffu, lo, o);
+                            ff_add_ff(hi, lo, h2, l2);
+                        }
+                        out[c] = static_cast<double>(hi) + static_cast<double>(lo);
+                    }
+                    const int64_t i = oidx[q];
+                    if (lane == 0 && row_ok(d, sp, i, p.status)) {
+                        if (d.n_split == 1) {
+                            for (int c = 0; c < 3; c++) { d.F[3 * i + c] = out[c]; d.J[3 * i + c] = out[3 + c]; }
+                            if (POT && d.pot) d.pot[i] = out[6];
+                        } else {
+                            // the split slot holds float-float pairs, as written by write_item_ff
+                            float2 *o8 = reinterpret_cast<float2 *>(d.pF + (static_cast<int64_t>(sp) * d.n_act + i) * 8);
+                            for (int c = 0; c < 7; c++) {
+                                const float h = c < NC ? __double2float_rn(out[c]) : 0.f;
+                                const float l = c < NC ? __double2float_rn(out[c] - static_cast<double>(h)) : 0.f;
+                                o8[c] = make_float2(h, l);
+                            }
                         }
                     }
                 }
@@ -257,12 +302,11 @@ __global__ void __launch_bounds__((WC + NL) * 32, 1) regf3ws_kernel(const RegfPa
     } else {
         // --------------------------------------------------------------- list warps
         const int lw = warp - WC;   // serves compute warps lw, lw + NL, lw + 2 NL, ...
-        for (int64_t item = blockIdx.x; item < p.n_items && !aborted; item += gridDim.x) {
-            if (lane == 0) d = p.table ? p.table[find_cluster(p, item)] : p.d0;
+        for (int64_t pos = blockIdx.x; pos < p.n_items && !aborted; pos += gridDim.x) {
+            int cl, ib, sp;
+            if (!item_at(p, pos, cl, ib, sp)) continue;
+            if (lane == 0) d = p.work ? p.table[cl] : p.d0;
             __syncwarp();
-            const int64_t local = item - d.item_begin;
-            const int ib = static_cast<int>(local / d.n_split);
-            const int sp = static_cast<int>(local - static_cast<int64_t>(ib) * d.n_split);
             const int tb = sp * d.tiles_per_split;
             const int te = min(tb + d.tiles_per_split, d.n_tiles);
             int32_t *row[NCW][I];
