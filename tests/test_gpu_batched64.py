@@ -28,6 +28,17 @@ def cfg4():
     return inputs.cached(inputs.config4)
 
 
+@pytest.fixture(scope="module")
+def cfg4_oracle(cfg4):
+    """Oracle outputs and term-length sums (force, jerk) of every cluster."""
+    res = []
+    for w in cfg4:
+        x, v = oracle_predicted(w)
+        SF, SJ = oracle.regular_mag(x, v, w.m, w.act, w.h)
+        res.append((oracle_run(w), SF, SJ))
+    return res
+
+
 def _setup(ctx, ws, offs):
     keep, cl = [], []
     for w, off in zip(ws, offs):
@@ -46,7 +57,7 @@ def _host(keep):
     return [{k: v.cpu().numpy() for k, v in out.items() if v is not None} for _, out in keep]
 
 
-def test_batched64_tuned_graph_matches_oracle_and_per_cluster_calls(cfg4):
+def test_batched64_tuned_graph_matches_oracle_and_per_cluster_calls(cfg4, cfg4_oracle):
     import torch
     ws = cfg4
     assert len(ws) == 64
@@ -85,12 +96,10 @@ def test_batched64_tuned_graph_matches_oracle_and_per_cluster_calls(cfg4):
         assert ctx.sync_status() == 0
         single = _host(keep)
     beyond = []
-    for c, (w, g, s) in enumerate(zip(ws, graph, single)):
+    for c, (w, g, s, (o, SF, SJ)) in enumerate(zip(ws, graph, single, cfg4_oracle)):
         for k in ("nnb", "list", "ovf"):
             assert np.array_equal(g[k], s[k]), k
-        x, v = oracle_predicted(w)
-        SF, SJ = oracle.regular_mag(x, v, w.m, w.act, w.h)
-        beyond += [(c,) + r for r in compare_conditioned(g, oracle_run(w), SF, SJ, w.cap, "mixed")]
+        beyond += [(c,) + r for r in compare_conditioned(g, o, SF, SJ, w.cap, "mixed")]
     print(f"64 clusters, {sum(w.n_act for w in ws)} rows: {len(beyond)} beyond the relative bar, within u*S:")
     for r in beyond:
         print("  cluster %d row %d: force %.2e (cond %.0f), jerk %.2e (cond %.0f)" % r)
@@ -111,3 +120,33 @@ def test_batched64_fp64_plan_meets_the_relative_bar_on_every_row(cfg4):
         got = _host(keep)
     for w, g in zip(ws, got):
         compare(g, oracle_run(w), w.cap, "fp64")
+
+
+# Short j-splits make a plan of many more work items than CTAs, of mixed
+# lengths (a cluster's last split is shorter), which the host deals to the
+# CTAs longest first: the CTAs then run different numbers of items and leave
+# the last slots of their work list empty, and every split cluster goes
+# through the merge.  One tiling per kernel family: the list-warp kernel, the
+# j-pair kernel with inline lists, and the scalar per-particle kernel.
+@pytest.mark.parametrize("cfg", [(16, 2, 1024, 3, 9), (16, 2, 1024, 4, 5), (8, 2, 512, 6, 0)],
+                         ids=["list-warps-3-tiles", "j-pair-4-tiles", "scalar-6-tiles"])
+def test_batched64_split_plans_match_oracle(cfg4, cfg4_oracle, cfg):
+    ws = cfg4
+    offs = np.cumsum([0] + [w.n + (w.n % 2) for w in ws])
+    with Context(int(offs[-1])) as ctx:
+        keep, cl = _setup(ctx, ws, offs)
+        plan = B.nb_plan_create(ctx.h, cl, B.NB_MIXED, B.nb_kcfg(*cfg))
+        try:
+            assert B.nb_plan_get_config(plan).as_tuple() == cfg
+            assert B.nb_plan_launches(plan) == 2   # the force kernel and the merge
+            for _, out in keep:
+                out["F"].zero_(); out["list"].fill_(-1); out["nnb"].fill_(-5)
+            B.nb_plan_run(plan, ctx=ctx.h)
+            assert ctx.sync_status() == 0
+            got = _host(keep)
+        finally:
+            B.nb_plan_destroy(plan)
+    beyond = 0
+    for w, g, (o, SF, SJ) in zip(ws, got, cfg4_oracle):
+        beyond += len(compare_conditioned(g, o, SF, SJ, w.cap, "mixed"))
+    assert beyond <= 20
