@@ -50,7 +50,10 @@ def parse_args():
     ap.add_argument("--n-act", type=int, default=0, help="active particles (0 = all)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-forms", action="store_true", help="skip the FP64/FP32 side measurements")
-    ap.add_argument("--cpu-sample", type=int, default=4096, help="active particles in the oracle sample")
+    ap.add_argument("--cpu-sample", type=int, default=8192, help="active particles in the oracle sample")
+    ap.add_argument("--accuracy-rows", default="all", choices=["all", "sample"],
+                    help="rows of the accuracy check against the oracle: every active particle (about 15 s "
+                         "of host work at N = n_act = 131072), or the timed CPU-baseline sample")
     ap.add_argument("--no-e2e", action="store_true", help="skip the host-buffer measurement")
     ap.add_argument("--no-side", action="store_true",
                     help="skip the compact side workloads of the default line (batched clusters, offset cluster "
@@ -571,7 +574,18 @@ def run_ours(args):
     if not args.no_cpu_baseline and world == 1:
         base, o, rows = cpu_baseline(w, args.cpu_sample)
         line["cpu_baseline"] = base
+        acc_note = f"the {len(rows)} rows of the CPU-baseline sample"
+        if args.accuracy_rows == "all" and len(rows) < w.n_act:
+            import numpy as np
+
+            import oracle
+            t0 = time.perf_counter()
+            x, v = oracle.predict(w.x0, w.v0, w.a0, w.adot0, w.t0, w.t)
+            o = oracle.regular(x, v, w.m, w.act, w.h, cap=w.cap, threads=oracle.default_threads())
+            rows = np.arange(w.n_act)
+            acc_note = f"every one of the {w.n_act} active rows (oracle {time.perf_counter() - t0:.1f} s)"
         line["accuracy_vs_oracle"] = {m: accuracy(g, o, rows, w.cap) for m, g in outs.items()}
+        line["accuracy_vs_oracle"]["rows"] = acc_note
     if not args.no_side and world == 1:
         line.update(side_workloads(args, peak))
     if world > 1:
