@@ -13,8 +13,8 @@ import pytest
 
 import oracle
 from paper_1205_1222_gb300 import Context, binding as B, build, inputs, mode_id
-from tests.gpu_util import (TOL, compare, dev, direct_sum_accel, gpu_run, list_mismatches, oracle_predicted,
-                            oracle_run, rel_err, upload)
+from tests.gpu_util import (TOL, compare, compare_conditioned, dev, direct_sum_accel, gpu_run, list_mismatches,
+                            oracle_predicted, oracle_run, rel_err, upload)
 
 pytestmark = pytest.mark.gpu
 
@@ -495,6 +495,62 @@ def test_batched_plan_with_mixed_flags(mode, odd):
                 compare(g, oracle_run(w, pot=q), w.cap, mode, pot=q)
         finally:
             B.nb_plan_destroy(plan)
+
+
+# Degenerate clusters in one plan: no active particle, one particle active,
+# j-ranges of 5, 63, 64 and 65 slots (a single part-filled step), of 1023, 1024
+# and 1025 (a tile boundary, the last tile holding one j) and 2049, a list cap
+# that overflows, at even and odd slot offsets.  Every tiling family serves
+# it, including j-splits of one tile, whose work lists leave CTAs with
+# different item counts.
+_EDGE = [(5, 5, 8), (63, 63, 16), (64, 1, 16), (65, 7, 16), (700, 0, 16), (1023, 500, 16),
+         (1024, 1, 16), (1025, 1025, 4), (2049, 33, 16)]
+
+
+@pytest.mark.parametrize("cfg,odd", [(None, False), (None, True), ((16, 2, 1024, 1, 9), False),
+                                     ((16, 2, 1024, 1, 5), False), ((16, 2, 512, 2, 5), False),
+                                     ((8, 2, 512, 1, 0), True)],
+                         ids=["default-even", "default-odd", "list-warps-1-tile", "j-pair-1-tile",
+                              "j-pair-512-2-tiles", "scalar-odd-1-tile"])
+def test_plan_of_degenerate_clusters(cfg, odd):
+    ws = []
+    for c, (n, na, cap) in enumerate(_EDGE):
+        act = np.sort(np.random.default_rng(300 + c).choice(n, max(na, 1), replace=False)).astype(np.int32)
+        ws.append(inputs.cluster(n, 310 + c, min(8, n - 2), cap, act=act))
+    gaps = [w.n + 3 for w in ws]
+    offs = np.cumsum([0] + gaps)
+    offs = offs + 1 if odd else offs + (offs % 2)
+    with Context(int(offs[-1]) + 1) as ctx:
+        keep, cl = [], []
+        for (n, na, cap), w, off in zip(_EDGE, ws, offs):
+            d = upload(w)
+            ctx.predict(d["x0"], d["v0"], d["a0"], d["adot0"], d["m"], d["t0"], w.t, offset=int(off))
+            out = ctx.alloc_outputs(max(na, 1), w.cap)
+            keep.append((d, out))
+            cl.append(B.nb_cluster(int(off), w.n, na, w.cap, d["act"].data_ptr(), d["h"].data_ptr(), None,
+                                   out["F"].data_ptr(), out["J"].data_ptr(), None, out["nnb"].data_ptr(),
+                                   out["list"].data_ptr(), out["ovf"].data_ptr()))
+        plan = B.nb_plan_create(ctx.h, cl, B.NB_MIXED, None if cfg is None else B.nb_kcfg(*cfg))
+        try:
+            if cfg is not None:
+                assert B.nb_plan_get_config(plan).as_tuple() == cfg
+            for _, out in keep:
+                out["F"].fill_(7.0); out["list"].fill_(-1); out["nnb"].fill_(-5)
+            B.nb_plan_run(plan, ctx=ctx.h)
+            assert ctx.sync_status() == 0
+            got = [{k: v.cpu().numpy() for k, v in out.items() if v is not None} for _, out in keep]
+        finally:
+            B.nb_plan_destroy(plan)
+    for (n, na, cap), w, g in zip(_EDGE, ws, got):
+        if na == 0:
+            assert g["nnb"][0] == -5 and np.all(g["F"][0] == 7.0)   # nothing written for an empty active set
+            continue
+        x, v = oracle_predicted(w)
+        SF, SJ = oracle.regular_mag(x, v, w.m, w.act, w.h)
+        o = oracle_run(w)
+        compare_conditioned(g, o, SF, SJ, w.cap, "mixed")
+        if n == 1025:
+            assert np.any(o["ovf"] == 1)   # the cap of 4 overflows
 
 
 # ------------------------------------------------------------- host step
