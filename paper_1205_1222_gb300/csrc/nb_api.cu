@@ -1443,6 +1443,19 @@ int nb_plan_create(nb_ctx *ctx, int32_t n_clusters, const nb_cluster *cl, int mo
             per[l.second].push_back(static_cast<int32_t>(k));
             heap.push({l.first + its[k].tiles + 1, l.second});
         }
+        // Each CTA runs its items alternately from the long and the short end.
+        // A short item carries as many list entries per particle as a long
+        // one in far fewer tiles; between two long items the list warps
+        // catch up on it while the compute warps run on.
+        for (auto &v : per) {
+            std::vector<int32_t> alt;
+            alt.reserve(v.size());
+            for (size_t a = 0, b = v.size(); a < b;) {
+                alt.push_back(v[a++]);
+                if (a < b) alt.push_back(v[--b]);
+            }
+            v.swap(alt);
+        }
         size_t most = 0;
         for (const auto &v : per) most = std::max(most, v.size());
         p->n_slots = static_cast<int64_t>(most) * G;
