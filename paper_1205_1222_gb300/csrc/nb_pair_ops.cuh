@@ -110,6 +110,15 @@ __device__ __forceinline__ uint64_t reduce_or_bits(uint64_t b)
     return (static_cast<uint64_t>(hi) << 32) | lo;
 }
 __device__ __forceinline__ int lowest_bit(uint32_t b) { return __ffs(b) - 1; }
+
+// The flag bit of j-offset o within a tile of JT j (bit 2 u + h of lane L for
+// o = 2 (32 u + L) + h), on the lane that holds it, else 0: a particle's own
+// slot is flagged by the pair terms (r^2 = 0 < h^2) and cleared with this.
+template <class Bits>
+__device__ __forceinline__ Bits self_bit(int o, int jt, int lane)
+{
+    return (o >= 0 && o < jt && ((o >> 1) & 31) == lane) ? (Bits(1) << (2 * (o >> 6) + (o & 1))) : Bits(0);
+}
 __device__ __forceinline__ int lowest_bit(uint64_t b) { return __ffsll(static_cast<long long>(b)) - 1; }
 
 // Position in the CTA's sequence of j-tiles: the slot of the work item, the

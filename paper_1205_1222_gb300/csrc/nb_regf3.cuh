@@ -555,29 +555,30 @@ __global__ void __launch_bounds__(W * 32, MINB) regf3_kernel(const RegfParams p)
 
             // Neighbour lists of the tile, in ascending j: for each i-particle,
             // the flagged units in order; within a unit the order is (lane, half).
+            {
+                const int cap = d.cap;
+                const unsigned lt = lanemask_lt();
 #pragma unroll
-            for (int q = 0; q < I; q++) {
-                Bits todo = reduce_or_bits(bits[q]);
-                while (todo) {
-                    const int unit = lowest_bit(todo) >> 1;
-                    todo &= ~(Bits(3) << (2 * unit));
-                    const int pl = unit * 32 + lane;
-                    const bool fa = (bits[q] >> (2 * unit)) & 1u, fb = (bits[q] >> (2 * unit + 1)) & 1u;
-                    const int ja = jt0 + 2 * pl;
-                    const int gq = myrec[q].gi;
-                    const bool xa = fa && ja != gq, xb = fb && ja + 1 != gq;
-                    const unsigned ma = __ballot_sync(0xffffffffu, xa);
-                    const unsigned mb = __ballot_sync(0xffffffffu, xb);
-                    const unsigned lt = lanemask_lt();
-                    const int pa = cnt[q] + __popc(ma & lt) + __popc(mb & lt);
-                    const int pb = pa + (xa ? 1 : 0);
-                    const int cap = d.cap;
-                    if ((xa && pa < cap) || (xb && pb < cap)) {
-                        int32_t *row = myrec[q].row;
+                for (int q = 0; q < I; q++) {
+                    const Bits b = bits[q] & ~self_bit<Bits>(myrec[q].gi - jt0, JT, lane);   // the particle itself
+                    Bits todo = reduce_or_bits(b);
+                    if (!todo) continue;
+                    int32_t *const row = myrec[q].row;
+                    int n = cnt[q];
+                    while (todo) {
+                        const int unit = lowest_bit(todo) >> 1;
+                        todo &= ~(Bits(3) << (2 * unit));
+                        const int ja = jt0 + 2 * (unit * 32 + lane);
+                        const bool xa = (b >> (2 * unit)) & 1u, xb = (b >> (2 * unit + 1)) & 1u;
+                        const unsigned ma = __ballot_sync(0xffffffffu, xa);
+                        const unsigned mb = __ballot_sync(0xffffffffu, xb);
+                        const int pa = n + __popc(ma & lt) + __popc(mb & lt);
+                        const int pb = pa + (xa ? 1 : 0);
                         if (xa && pa < cap) row[pa] = ja;
                         if (xb && pb < cap) row[pb] = ja + 1;
+                        n += __popc(ma) + __popc(mb);
                     }
-                    cnt[q] += __popc(ma) + __popc(mb);
+                    cnt[q] = n;
                 }
             }
 

@@ -199,25 +199,27 @@ __global__ void __launch_bounds__(W * 32, 1) regf_cl_kernel(const RegfParams p)
         if (t + 1 < te) issue_tile(t + 1);
 
         // neighbour lists of the tile into this CTA's segments, ascending j
+        const unsigned lt = lanemask_lt();
 #pragma unroll
         for (int q = 0; q < I; q++) {
-            Bits todo = reduce_or_bits(bits[q]);
+            const Bits b = bits[q] & ~self_bit<Bits>(gi[q] - jt0, JT, lane);   // the particle itself
+            Bits todo = reduce_or_bits(b);
             int32_t *row = s_list + (warp * I + q) * cap;
+            int n = cnt[q];
             while (todo) {
                 const int unit = lowest_bit(todo) >> 1;
                 todo &= ~(Bits(3) << (2 * unit));
                 const int ja = jt0 + 2 * (unit * 32 + lane);
-                const bool fa = (bits[q] >> (2 * unit)) & 1u, fb = (bits[q] >> (2 * unit + 1)) & 1u;
-                const bool xa = fa && ja != gi[q], xb = fb && ja + 1 != gi[q];
+                const bool xa = (b >> (2 * unit)) & 1u, xb = (b >> (2 * unit + 1)) & 1u;
                 const unsigned ma = __ballot_sync(0xffffffffu, xa);
                 const unsigned mb = __ballot_sync(0xffffffffu, xb);
-                const unsigned lt = lanemask_lt();
-                const int pa = cnt[q] + __popc(ma & lt) + __popc(mb & lt);
+                const int pa = n + __popc(ma & lt) + __popc(mb & lt);
                 const int pb = pa + (xa ? 1 : 0);
                 if (xa && pa < cap) row[pa] = ja;
                 if (xb && pb < cap) row[pb] = ja + 1;
-                cnt[q] += __popc(ma) + __popc(mb);
+                n += __popc(ma) + __popc(mb);
             }
+            cnt[q] = n;
         }
 
         auto fold = [&](int c) {
