@@ -230,9 +230,14 @@ int nb_get_frame(nb_ctx *ctx, double *u);
  * nnb is the true count, ovf[k] = (nnb[k] > cap).  A pair at exactly |R| = h
  * is not a neighbour.  Pairs with |R_ij| = 0 (j != i) outside the sphere are
  * undefined input.  mode: NB_FP64, NB_MIXED or NB_FP32; the matching form
- * must have been predicted (NB_ERR_STATE otherwise).  May grow the context's
- * split scratch with cudaMalloc (call nb_reserve() first to avoid that, e.g.
- * before stream capture).  Errors: NB_ERR_ARG for out-of-range sizes, NULL
+ * must have been predicted (NB_ERR_STATE otherwise).  The call is one
+ * persistent kernel launch, plus a merge launch when its j-range is split; a
+ * call whose blocks of active particles fill some rounds of the grid and part
+ * of another, with the split left to the library, may run as two launches
+ * (the whole rounds unsplit, then the remaining rows with a split j-range and
+ * their merge); nb_last_launches reports the count.  May grow the context's
+ * split scratch with cudaMalloc (call nb_reserve() with nb_scratch_bytes()
+ * first to avoid that, e.g. before stream capture).  Errors: NB_ERR_ARG for out-of-range sizes, NULL
  * outputs, mode; invalid act/h values found on the device set
  * NB_ERR_DEVICE_INPUT in the status word (those particles get no result). */
 int nb_regular_force(nb_ctx *ctx, int64_t j_begin, int64_t n_j, int32_t n_act,
@@ -249,7 +254,8 @@ int nb_regular_force(nb_ctx *ctx, int64_t j_begin, int64_t n_j, int32_t n_act,
  * never allocates or frees anything.  Instead its split partials live in one
  * fixed device array of 32 MiB (33554432 bytes) that every GPU loading the
  * library holds until the process exits.  A call with n_split j-splits needs
- * about n_split * n_act * (68 + 4 * cap) bytes of it (no split, no scratch).
+ * about n_split * n_act * (68 + 4 * cap) bytes of it (no split, no scratch;
+ * for a call run as two parts, n_act is the rows of the split part).
  * Same arguments, outputs and errors as nb_regular_force, and the same tiling
  * (the one nb_set_kernel_config chose, else the tuned one of the call's size
  * class, else the default), so the two calls give bit-identical results; plus:

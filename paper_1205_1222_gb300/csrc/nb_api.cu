@@ -572,7 +572,7 @@ int launch_regf(nb_ctx *ctx, const KernelEntry &e, const nb::RegfParams &p, int6
 // default when it names the cluster kernel for a split count, cap or cluster
 // size that kernel cannot take.
 int select_single(nb_ctx *ctx, const Call &c, const nb_kcfg *cfg_override, int *idx_out, int *occ_out,
-                  ClusterDesc *d_out)
+                  ClusterDesc *d_out, bool *heuristic_out = nullptr)
 {
     const int flags = (c.dtr ? 1 : 0) | (c.pot ? 2 : 0);
     nb_kcfg cfg = cfg_override ? *cfg_override : pick_cfg(ctx, c.mode, flags, c.n_act, c.n_j);
@@ -597,10 +597,120 @@ int select_single(nb_ctx *ctx, const Call &c, const nb_kcfg *cfg_override, int *
         *idx_out = idx;
         *occ_out = occ;
         *d_out = d;
+        if (heuristic_out) *heuristic_out = cfg.split <= 0;
         return NB_OK;
     }
     ctx->err = "no kernel for this call";
     return NB_ERR_UNSUPPORTED;
+}
+
+// A single call whose i-blocks fill at least one round of the persistent grid
+// but not a whole number of rounds may run as two launches over consecutive
+// rows of its active set: the i-blocks of the whole rounds with their j-ranges
+// unsplit, then the remaining i-blocks with their j-ranges split so that they
+// fill one round together (and a merge of their splits).  With the uniform
+// split every i-block pays for the round that the remainder leaves part-filled
+// (at 16384 of N = 16384 active, 512 i-blocks of 32 take four rounds of 152
+// CTAs, the last 37 % full).  Taken only where the split is left to the
+// heuristic and the cost model of tile_cluster (rounds x (tiles per item + 1.5)
+// plus the merge, here plus half a tile for the second launch) puts it below
+// the uniform split; not for the framed or the thread-block-cluster kernels.
+// Returns the rows of the unsplit part (0: run the call whole) and the tiles
+// per split of the rest.
+struct TailSplit {
+    int32_t rows;
+    int32_t tps;
+};
+
+TailSplit tail_split(const KernelEntry &e, int occ, int sm, const ClusterDesc &d, bool heuristic)
+{
+    TailSplit t{0, 0};
+    if (!heuristic || e.packed < 2 || e.packed == 4 || e.packed == kClusterPacked || d.n_tiles < 2) return t;
+    const int64_t slots = std::max<int64_t>(1, static_cast<int64_t>(sm) * occ);
+    const int64_t full = d.n_iblk / slots, rem = d.n_iblk - full * slots;
+    if (full < 1 || rem == 0) return t;
+    const int64_t ipb = iblock_size(e);
+    const int64_t head_rows = full * slots * ipb, tail_rows = d.n_act - head_rows;
+    const int S = static_cast<int>(std::min<int64_t>(std::max<int64_t>(slots / rem, 1), d.n_tiles));
+    const int ts = (d.n_tiles + S - 1) / S;
+    const int64_t ns = (d.n_tiles + ts - 1) / ts;
+    if (tail_rows <= 0) return t;
+    if (ns > 1 && ns * tail_rows * (72 + 4 * static_cast<int64_t>(d.cap)) > (int64_t(1) << 30)) return t;
+    auto merge = [&](int64_t n_split, int64_t rows) {
+        return n_split > 1 ? 1.5 + static_cast<double>(n_split) * rows * (64.0 + 2.0 * d.cap) / 2e7 : 0.0;
+    };
+    const int64_t items = static_cast<int64_t>(d.n_iblk) * d.n_split;
+    const double uniform = static_cast<double>((items + slots - 1) / slots) * (d.tiles_per_split + 1.5) +
+                           merge(d.n_split, d.n_act);
+    const double tail = static_cast<double>(full) * (d.n_tiles + 1.5) + (ts + 1.5) + merge(ns, tail_rows) + 0.5;
+    if (tail < uniform - 1e-9) {
+        t.rows = static_cast<int32_t>(head_rows);
+        t.tps = ts;
+    }
+    return t;
+}
+
+// The two parts of a tail-split call: rows [0, t.rows) with one split, the
+// rest (the call's pointers moved on by t.rows rows) with t.tps tiles per split.
+void tail_parts(const KernelEntry &e, int occ, int sm, const Call &c, const TailSplit &t, ClusterDesc &head,
+                ClusterDesc &rest)
+{
+    Call ch = c;
+    ch.n_act = t.rows;
+    head = make_desc(ch);
+    const int32_t n_tiles = static_cast<int32_t>((c.n_j + e.jtile - 1) / e.jtile);
+    nb_kcfg fh{e.warps, e.ipw, e.jtile, std::max(1, n_tiles), e.packed};
+    tile_cluster(e, occ, sm, &fh, head);
+    Call cr = c;
+    const int64_t r = t.rows;
+    cr.n_act = c.n_act - t.rows;
+    cr.act = c.act + r;
+    cr.h = c.h + r;
+    cr.dtr = c.dtr ? c.dtr + r : nullptr;
+    cr.F = c.F + 3 * r;
+    cr.J = c.J + 3 * r;
+    cr.pot = c.pot ? c.pot + r : nullptr;
+    cr.nnb = c.nnb + r;
+    cr.list = c.list ? c.list + r * c.cap : nullptr;
+    cr.ovf = c.ovf + r;
+    rest = make_desc(cr);
+    nb_kcfg fr{e.warps, e.ipw, e.jtile, t.tps, e.packed};
+    tile_cluster(e, occ, sm, &fr, rest);
+    head.item_begin = rest.item_begin = 0;
+}
+
+// Launch the force kernel of one part of a single call (its split scratch
+// already carved), and the merge of its splits; counts the launches.
+int launch_part(nb_ctx *ctx, const KernelEntry &e, int occ, const ClusterDesc &d, int mode, cudaStream_t st,
+                int *launches)
+{
+    nb::RegfParams p{};
+    p.js = tile_streams(ctx, mode, e);
+    p.soa = jset(ctx, mode);
+    p.d0 = d;
+    p.table = nullptr;
+    p.work = nullptr;
+    p.n_clusters = 1;
+    p.n_items = static_cast<int64_t>(d.n_iblk) * d.n_split;
+    p.status = ctx->d_status;
+    p.wait_ns = ctx->wait_ns;
+    p.extra_tx = ctx->extra_tx;
+    const int64_t grid = std::min<int64_t>(p.n_items, static_cast<int64_t>(ctx->sm_count) * occ);
+    int rc = launch_regf(ctx, e, p, grid, st);
+    if (rc != NB_OK) return rc;
+    ++*launches;
+    if (d.n_split > 1 && e.packed != kClusterPacked) {
+        nb::MergeParams mp{};
+        mp.d0 = d;
+        mp.n_clusters = 1;
+        mp.n_total = d.n_act;
+        mp.ff = mode != NB_FP64;
+        mp.status = ctx->d_status;
+        nb::launch_merge(mp, st);
+        NB_CUDA(ctx, cudaGetLastError());
+        ++*launches;
+    }
+    return NB_OK;
 }
 
 int run_single(nb_ctx *ctx, const Call &c, const nb_kcfg *cfg_override, cudaStream_t st)
@@ -612,9 +722,24 @@ int run_single(nb_ctx *ctx, const Call &c, const nb_kcfg *cfg_override, cudaStre
     DeviceGuard guard(ctx->device);
     int idx = -1, occ = 0;
     ClusterDesc d{};
-    rc = select_single(ctx, c, cfg_override, &idx, &occ, &d);
+    bool heuristic = false;
+    rc = select_single(ctx, c, cfg_override, &idx, &occ, &d, &heuristic);
     if (rc != NB_OK) return rc;
     const KernelEntry &e = registry().all[idx];
+    const TailSplit tail = tail_split(e, occ, ctx->sm_count, d, heuristic);
+    if (tail.rows > 0) {
+        ClusterDesc head{}, rest{};
+        tail_parts(e, occ, ctx->sm_count, c, tail, head, rest);
+        rc = grow_scratch(ctx, cluster_scratch(rest, e.packed), st);
+        if (rc != NB_OK) return rc;
+        carve_scratch(head, nullptr, e.packed);
+        carve_scratch(rest, static_cast<char *>(ctx->scratch), e.packed);
+        int launches = 0;
+        rc = launch_part(ctx, e, occ, head, c.mode, st, &launches);
+        if (rc == NB_OK) rc = launch_part(ctx, e, occ, rest, c.mode, st, &launches);
+        ctx->last_launches = launches;
+        return rc;
+    }
     rc = grow_scratch(ctx, cluster_scratch(d, e.packed), st);
     if (rc != NB_OK) return rc;
     carve_scratch(d, static_cast<char *>(ctx->scratch), e.packed);
@@ -938,8 +1063,19 @@ size_t nb_scratch_bytes(nb_ctx *ctx, int64_t n_j, int32_t n_act, int32_t cap, in
         d.n_j = static_cast<int32_t>(n_j);
         d.n_act = n_act;
         d.cap = cap;
-        tile_cluster(registry().all[idx], occ, ctx->sm_count, &cfg, d);
-        best = std::max(best, cluster_scratch(d, registry().all[idx].packed));
+        const KernelEntry &e = registry().all[idx];
+        tile_cluster(e, occ, ctx->sm_count, &cfg, d);
+        best = std::max(best, cluster_scratch(d, e.packed));
+        const TailSplit t = tail_split(e, occ, ctx->sm_count, d, cfg.split <= 0);
+        if (t.rows > 0) {   // the split part of a tail-split call
+            ClusterDesc r{};
+            r.n_j = d.n_j;
+            r.n_act = n_act - t.rows;
+            r.cap = cap;
+            const nb_kcfg fr{e.warps, e.ipw, e.jtile, t.tps, e.packed};
+            tile_cluster(e, occ, ctx->sm_count, &fr, r);
+            best = std::max(best, cluster_scratch(r, e.packed));
+        }
     }
     return best;
 }
@@ -1752,9 +1888,13 @@ extern "C" int nb_regular_force_noalloc(nb_ctx *ctx, int64_t j_begin, int64_t n_
     // the tuned one of the call's size class, else the default
     int idx = -1, occ = 0;
     ClusterDesc d{};
-    rc = select_single(ctx, c, nullptr, &idx, &occ, &d);
+    bool heuristic = false;
+    rc = select_single(ctx, c, nullptr, &idx, &occ, &d, &heuristic);
     if (rc != NB_OK) return rc;
     const KernelEntry &e = registry().all[idx];
+    const TailSplit tail = tail_split(e, occ, ctx->sm_count, d, heuristic);
+    ClusterDesc head{};
+    if (tail.rows > 0) tail_parts(e, occ, ctx->sm_count, c, tail, head, d);   // d: the split part
     const size_t need = cluster_scratch(d, e.packed);
     if (need > kNoAllocScratchBytes) {
         ctx->err = "the call needs " + std::to_string(need) + " bytes of split scratch; the fixed array of "
@@ -1766,30 +1906,13 @@ extern "C" int nb_regular_force_noalloc(nb_ctx *ctx, int64_t j_begin, int64_t n_
     // every work item stores (does not add to) its own (split, particle)
     // partials, count and list slots, and the merge reads only those.
     carve_scratch(d, static_cast<char *>(scratch), e.packed);
-
-    nb::RegfParams p{};
-    p.js = tile_streams(ctx, c.mode, e);
-    p.soa = jset(ctx, c.mode);
-    p.d0 = d;
-    p.n_clusters = 1;
-    p.n_items = static_cast<int64_t>(d.n_iblk) * d.n_split;
-    p.status = ctx->d_status;
-    p.wait_ns = ctx->wait_ns;
-    p.extra_tx = ctx->extra_tx;
-    const int64_t grid = std::min<int64_t>(p.n_items, static_cast<int64_t>(ctx->sm_count) * occ);
-    rc = launch_regf(ctx, e, p, grid, st);
-    if (rc != NB_OK) return rc;
-    ctx->last_launches = 1;
-    if (d.n_split > 1 && e.packed != kClusterPacked) {
-        nb::MergeParams mp{};
-        mp.d0 = d;
-        mp.n_clusters = 1;
-        mp.n_total = d.n_act;
-        mp.ff = c.mode != NB_FP64;
-        mp.status = ctx->d_status;
-        nb::launch_merge(mp, st);
-        NB_CUDA(ctx, cudaGetLastError());
-        ctx->last_launches = 2;
+    int launches = 0;
+    if (tail.rows > 0) {   // the unsplit rounds first, as nb_regular_force runs them
+        carve_scratch(head, nullptr, e.packed);
+        rc = launch_part(ctx, e, occ, head, c.mode, st, &launches);
+        if (rc != NB_OK) return rc;
     }
-    return NB_OK;
+    rc = launch_part(ctx, e, occ, d, c.mode, st, &launches);
+    ctx->last_launches = launches;
+    return rc;
 }

@@ -85,6 +85,25 @@ def test_noalloc_takes_the_tuned_tiling(workload):
         compare(ref, default, w.cap, "mixed")
 
 
+def test_noalloc_matches_a_tail_split_call(workload):
+    """A call of whole rounds of the persistent grid plus a remainder (every
+    particle of N = 16384 active, the list-warp tiling) runs as two parts, the
+    remainder with split j-ranges; the allocation-free call runs the same parts
+    with its fixed array for the splits: three launches and bit-identical
+    results, twice."""
+    w = inputs.cluster(16384, 78, 64, 256)
+    with Context(w.n) as ctx:
+        d = upload(w)
+        ctx.predict(d["x0"], d["v0"], d["a0"], d["adot0"], d["m"], d["t0"], w.t)
+        ctx.set_config("mixed", B.nb_kcfg(16, 2, 1024, 0, 9))
+        ref, ref_launches = _call(B.nb_regular_force, ctx, d, w, "mixed", w.cap)
+        assert ref_launches == 3
+        for _ in range(2):
+            got, launches = _call(B.nb_regular_force_noalloc, ctx, d, w, "mixed", w.cap)
+            assert launches == 3
+            _same(got, ref)
+
+
 def test_noalloc_rejects_a_call_beyond_its_fixed_scratch(workload):
     w = workload
     n_act = 4096
