@@ -277,7 +277,8 @@ int nb_regular_force_noalloc(nb_ctx *ctx, int64_t j_begin, int64_t n_j, int32_t 
 int nb_reserve(nb_ctx *ctx, size_t bytes);
 
 /* Scratch bytes a call of nb_regular_force with these sizes needs (0 when the
- * call needs no split).  Host only. */
+ * call needs no split; for a call that runs as two parts, the larger of the
+ * uniform split's need and the split part's).  Host only. */
 size_t nb_scratch_bytes(nb_ctx *ctx, int64_t n_j, int32_t n_act, int32_t cap, int mode);
 
 /* Batched form: the regular-force call for n_clusters independent clusters
