@@ -580,6 +580,47 @@ def test_tail_split_call():
     compare({k: v[:w.n_act] for k, v in g.items()}, oracle_run(w), w.cap, "mixed")
 
 
+def test_tail_split_call_captured_after_reserving_its_scratch():
+    """The scratch estimate of a call that runs as two parts is enough to
+    capture its first run in a CUDA graph: after nb_reserve(nb_scratch_bytes(..))
+    the capture needs no allocation, and two replays give an eager call's
+    outputs bit for bit (and the oracle's within the two-float tolerances)."""
+    import torch
+    n = 16384
+    w = inputs.cluster(n, 4243, 64, 256)
+    keys = ("F", "J", "nnb", "list", "ovf")
+    with Context(n) as ctx:
+        d = upload(w)
+        ctx.predict(d["x0"], d["v0"], d["a0"], d["adot0"], d["m"], d["t0"], w.t)
+        # the kernel's launch attributes, set by a call of the same tiling that needs no split scratch
+        ctx.set_config("mixed", B.nb_kcfg(16, 2, 1024, 16, 9))
+        ctx.regular_force(d["act"][:24], d["h"][:24], w.n, cap=w.cap, mode="mixed")
+        assert ctx.sync_status() == 0 and ctx.last_launches() == 1
+        ctx.set_config("mixed", B.nb_kcfg(16, 2, 1024, 0, 9))
+        need = ctx.scratch_bytes(w.n, w.n_act, w.cap, "mixed")
+        assert need > 0
+        ctx.reserve(need)
+        stream = torch.cuda.Stream()
+        stream.wait_stream(torch.cuda.current_stream())
+        out = ctx.alloc_outputs(w.n_act, w.cap)
+        torch.cuda.synchronize()
+        graph = torch.cuda.CUDAGraph()
+        with torch.cuda.stream(stream):
+            with torch.cuda.graph(graph, stream=stream):
+                ctx.regular_force(d["act"], d["h"], w.n, cap=w.cap, mode="mixed", out=out, stream=stream)
+        assert ctx.last_launches() == 3
+        for _ in range(2):
+            out["F"].zero_(); out["list"].fill_(-1); out["nnb"].fill_(-5)
+            graph.replay()
+            torch.cuda.synchronize()
+            assert ctx.sync_status() == 0
+        got = {k: out[k].cpu().numpy() for k in keys}
+        eager = gpu_run(w, "mixed", ctx=ctx)
+    for k in keys:
+        assert np.array_equal(got[k], eager[k]), k
+    compare(got, oracle_run(w), w.cap, "mixed")
+
+
 # ------------------------------------------------------------- host step
 
 def test_host_step_matches_oracle():
